@@ -1,0 +1,383 @@
+"""Benchmark of the HMC hot path on GB300.
+
+One step = one full molecular-dynamics trajectory on the 102x102 honeycomb
+torus with nt = 64 (1,331,712 space-time sites): pseudofermion creation for
+3 Hasenbusch masses (0.1, 0.5, 2.0), the nested Omelyan integrator with
+N_MD = 30 and time-scale ratios (6, 2, 2), forces from mixed-precision FGMRES
+solves (FP32 CG preconditioner, FP64 outer) at relative residual 1e-10, and
+the final action solves at 1e-12. Every M M^dagger application, CG and
+FGMRES iteration, force and MD update of the path runs in it.
+
+value = sites x (M M^dagger applications in the step) / step time, in Gsite/s:
+the operator throughput the whole path sustains. Inputs are resident in HBM
+before timing; L2 is flushed (256 MB write) between steps, outside the per-step
+CUDA-event windows. Also reported: FP64 CG vs mixed FGMRES time-to-solution on
+the same lattice, the roofline of the dominant kernel, an end-to-end figure with
+host buffers, and the CPU oracle timed on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs its own independent trajectories
+(replicas; no data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsite/s of M·M† apply (% HBM peak); solve ms @res 1e-10, mixed+batched vs FP64"
+UNIT = "Gsite/s"
+WORKLOAD = ("102x102 honeycomb torus, nt=64 (1,331,712 sites), kappa=1, U=3.8, beta=12: one "
+            "nested-Omelyan MD trajectory (N_MD=30, N_i=(6,2,2)) with 3 Hasenbusch masses "
+            "(0.1,0.5,2.0), mixed FP32/FP64 FGMRES forces at 1e-10")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        pw = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def cpu_oracle_apply(seconds: float):
+    """The oracle's M M^dagger on the same lattice, repeated for about `seconds`."""
+    import workloads as W
+    from oracle import fermion
+    from oracle.lattice import Lattice
+    w = W.workload("C5")
+    lat = Lattice.from_params(w.lat)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        fermion.apply_MMdag(lat, w.phi, 0.0, w.b)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return lat.N * reps / dt / 1e9, reps, dt
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle (numpy, complex128) as it stands, each step
+    a bounded sample of the same workload: oracle M M^dagger applications on
+    the 102x102x64 lattice for about 4 s."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_apply(0.5)
+    vals, tms = [], []
+    for _ in range(args.steps):
+        v, reps, dt = cpu_oracle_apply(4.0)
+        vals.append(v)
+        tms.append(dt * 1e3)
+    value = float(np.mean(vals))
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(tms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "oracle M M^dagger applications on the 102x102x64 lattice "
+                                   "(bounded sample of the trajectory's operator work)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "numpy complex128 oracle M M^dagger on 1,331,712 sites, ~4 s per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import paper_1804_07195_gb300 as hmc
+    from paper_1804_07195_gb300 import build
+    import workloads as W
+
+    build.build()
+    dev = torch.device("cuda", local)
+    w0 = W.workload("C5")
+    p = w0.lat
+    lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+    N = lat.nsites
+    masses = list(W.C5_MASSES)
+    integ = hmc.Integrator(0, W.C5_NMD, W.C5_NI, W.OMELYAN_ZETA, 1.0)
+    md_opts = hmc.SolverOpts(method=1, tol=1e-10)
+    act_opts = hmc.SolverOpts(method=1, tol=1e-12)
+
+    nsteps_total = args.warmup + args.steps + 1 + args.e2e_steps
+
+    def step_inputs(k):
+        g = W.rng([W.SEEDS["C5"], rank, k])
+        pi = W.draw_pi(g, N)
+        rho = [W.draw_complex(g, N) for _ in range(len(masses) + 1)]
+        return pi, rho
+
+    host_inputs = [step_inputs(k) for k in range(nsteps_total)]
+    phi0 = torch.tensor(w0.phi, device=dev)
+    dev_inputs = [(torch.tensor(pi, device=dev), [torch.tensor(r, device=dev) for r in rho])
+                  for pi, rho in host_inputs[: args.warmup + args.steps + 1]]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = hmc.Context(lat)
+    stream = torch.cuda.current_stream()
+
+    def trajectory(k, phi_t, pi_t, rho_t):
+        return ctx.md_trajectory(phi_t, pi_t, masses, rho_t, integ, md_opts, act_opts)
+
+    # warm-up
+    for k in range(args.warmup):
+        phi = phi0.clone()
+        pi, rho = dev_inputs[k]
+        trajectory(k, phi, pi.clone(), rho)
+    torch.cuda.synchronize()
+
+    # timed region
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    phis = [phi0.clone() for _ in range(args.steps)]
+    pis = [dev_inputs[args.warmup + k][0].clone() for k in range(args.steps)]
+    ctx.profile(False, reset=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    applies = 0
+    dH = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        H0, H1, info = trajectory(k, phis[k], pis[k], dev_inputs[args.warmup + k][1])
+        ev[k][1].record(stream)
+        applies += info["applies64"] + info["applies32"]
+        dH.append(H1 - H0)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    launches = ctx.profile_read()
+    gpu_launches = int(sum(v["launches"] for v in launches.values()))
+
+    # max over ranks of the time, sum of the work
+    sites_applied = float(N) * applies
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        s = torch.tensor([sites_applied], device=dev, dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        sites_applied = float(s.item())
+    value = sites_applied / (total_ms * 1e-3) / 1e9
+
+    # one extra step with CUDA events around every library launch: per-kernel
+    # durations for the roofline of the dominant kernel
+    ctx.profile(True, reset=True)
+    flush.zero_()
+    phi = phi0.clone()
+    pi, rho = dev_inputs[args.warmup + args.steps]
+    trajectory(-1, phi, pi.clone(), rho)
+    prof = ctx.profile_read()
+    ctx.profile(False, reset=True)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, dstat = dom
+    hbm, peak_kind = peaks()
+    bytes_launch = dstat["bytes"] / max(dstat["launches"], 1)
+    avg_s = dstat["ms"] / max(dstat["launches"], 1) * 1e-3
+    achieved = bytes_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    tot_prof_ms = sum(v["ms"] for v in prof.values())
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        if tj.get("kernel") == dname and tj.get("source_sha") == kernel_source_sha():
+            traffic = tj["bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": dname,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "launches_per_step": dstat["launches"], "avg_launch_us": avg_s * 1e6,
+                "share_of_kernel_time": dstat["ms"] / tot_prof_ms if tot_prof_ms else None,
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "algorithmic_bytes_per_site": bytes_launch / N,
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()
+                            if v["launches"]},
+                "method": "CUDA events around every launch on the context stream, one profiled "
+                          "trajectory after the timed region"}
+
+    # time-to-solution on the same lattice: plain FP64 CG vs mixed FGMRES
+    phi_t = phi0
+    b = dev_inputs[0][1][0]
+    solve = {}
+    for name, fn in (("fp64_cg", lambda: ctx.solve_cg(phi_t, 0.0, b, tol=1e-10)),
+                     ("mixed_fgmres", lambda: ctx.solve_fgmres(phi_t, 0.0, b, tol=1e-10))):
+        fn()
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, info = fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        solve[name] = {"ms": a.elapsed_time(z), "iters": info["iters"], "inner_iters": info["iters_inner"],
+                       "true_rel_res": info["true_rel_res"]}
+    solve["speedup_mixed_vs_fp64"] = solve["fp64_cg"]["ms"] / solve["mixed_fgmres"]["ms"]
+    solve["workload"] = "102x102x64 lattice, m_s=0, phi of the step, b = rho_0, true residual 1e-10"
+
+    # end to end through the public API with host buffers
+    e2e_val = None
+    h2d = d2h = 0
+    if args.e2e_steps > 0:
+        pinned = []
+        for k in range(args.e2e_steps):
+            pi, rho = host_inputs[args.warmup + args.steps + 1 + k]
+            pinned.append((torch.tensor(w0.phi).pin_memory(), torch.tensor(pi).pin_memory(),
+                           [torch.tensor(r).pin_memory() for r in rho]))
+        out_phi = torch.empty(N, dtype=torch.float64).pin_memory()
+        out_pi = torch.empty(N, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_app = 0
+        for ph_h, pi_h, rho_h in pinned:
+            ph_d = ph_h.to(dev, non_blocking=True)
+            pi_d = pi_h.to(dev, non_blocking=True)
+            rho_d = [r.to(dev, non_blocking=True) for r in rho_h]
+            H0, H1, info = ctx.md_trajectory(ph_d, pi_d, masses, rho_d, integ, md_opts, act_opts)
+            out_phi.copy_(ph_d, non_blocking=True)
+            out_pi.copy_(pi_d, non_blocking=True)
+            torch.cuda.synchronize()
+            e_app += info["applies64"] + info["applies32"]
+        dt = time.perf_counter() - t0
+        e2e_val = N * e_app / dt / 1e9
+        h2d = 8 * N * 2 + 16 * N * (len(masses) + 1)
+        d2h = 8 * N * 2 + 16
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
+        v, reps, dt = cpu_oracle_apply(args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"numpy complex128 oracle M M^dagger on the same 1,331,712-site lattice, "
+                         f"{reps} applications in {dt:.1f} s (single-threaded numpy)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write, untimed)",
+                           "sites": N, "mmdag_applies_per_step": applies / args.steps,
+                           "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": gpu_launches, "clocks": clk, "solve_ms": solve}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1804_07195_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -65,7 +65,9 @@ def force_kernel(lat: Lattice, phi: np.ndarray, eta: np.ndarray, w: np.ndarray) 
 
 
 class SolveA:
-    """x = (M_ms M_ms^dagger)^{-1} b by one of the oracle's solvers."""
+    """x = (M_ms M_ms^dagger)^{-1} b by one of the oracle's solvers:
+    "dense" (LU of the explicit M M^dagger), "splu" (sparse LU of M, then
+    x = M^{-dagger} (M^{-1} b)) or "cg"."""
 
     def __init__(self, lat: Lattice, method: str = "dense", tol: float = 1e-13):
         self.lat, self.method, self.tol = lat, method, tol
@@ -75,6 +77,10 @@ class SolveA:
         if self.method == "dense":
             Mx = fermion.dense_M(lat, phi, ms)
             return solvers.dense_solve(Mx @ Mx.conj().T, b)
+        if self.method == "splu":
+            import scipy.sparse.linalg as spla
+            lu = spla.splu(fermion.sparse_M(lat, phi, ms))
+            return lu.solve(lu.solve(b.astype(np.complex128)), trans="H")
         if self.method == "cg":
             res = solvers.cg(lambda v: fermion.apply_MMdag(lat, phi, ms, v), b, tol=self.tol)
             if not res.converged:

@@ -14,6 +14,7 @@ entry by entry from the same equation, as an independent restatement.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from .lattice import A, B, Lattice
 
@@ -100,6 +101,20 @@ def dense_M(lat: Lattice, phi: np.ndarray, ms: float) -> np.ndarray:
                     Mx[a, bb] += -dk
                     Mx[bb, a] += -dk
     return Mx
+
+
+def sparse_M(lat: Lattice, phi: np.ndarray, ms: float) -> sp.csc_matrix:
+    """M as a scipy sparse matrix: per row the diagonal entry, the time-hopping
+    entry at its time partner, and -delta kappa at each of the three hopping
+    partners (duplicates summed, as for n or m below 3)."""
+    rows = np.arange(lat.N)
+    tp, _ = lat.time_partner()
+    nb = lat.spatial_neighbours()
+    r = np.concatenate([rows, rows, np.repeat(rows, 3)])
+    c = np.concatenate([rows, tp, nb.ravel()])
+    v = np.concatenate([diagonal(lat).astype(np.complex128), time_hop(lat, phi, ms),
+                        np.full(3 * lat.N, -lat.delta * lat.kappa, dtype=np.complex128)])
+    return sp.csc_matrix((v, (r, c)), shape=(lat.N, lat.N))
 
 
 def free_spectrum(lat: Lattice, ms: float, theta: float = 0.0) -> np.ndarray:

@@ -1,0 +1,367 @@
+// C ABI entry points of libhmc: context management, argument validation,
+// operator applications, solves and instrumentation.
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "solvers.h"
+
+using namespace hmc;
+
+namespace hmc {
+
+hmc_status fail(hmc_ctx* c, hmc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+hmc_status cuda_fail(hmc_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return HMC_ERR_CUDA;
+}
+
+hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out) {
+  if (c->ws_bytes[slot] < bytes) {
+    if (c->ws[slot]) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->ws[slot]);
+      c->ws[slot] = nullptr;
+      c->ws_bytes[slot] = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HMC_ERR_NOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    c->ws[slot] = p;
+    c->ws_bytes[slot] = bytes;
+  }
+  *out = c->ws[slot];
+  return HMC_OK;
+}
+
+void prof_begin(hmc_ctx* c, int id, cudaEvent_t* a) {
+  c->prof.launches[id]++;
+  if (!c->prof.timing) return;
+  if (c->prof.free_events.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->prof.free_events.push_back(e);
+  }
+  *a = c->prof.free_events.back();
+  c->prof.free_events.pop_back();
+  cudaEventRecord(*a, c->stream);
+}
+
+static void prof_drain(hmc_ctx* c, size_t keep) {
+  // resolve the oldest pending pairs until at most `keep` remain
+  auto& P = c->prof.pending;
+  size_t n = P.size() > keep ? P.size() - keep : 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaEventSynchronize(P[i].b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P[i].a, P[i].b);
+    c->prof.ms[P[i].id] += ms;
+    c->prof.free_events.push_back(P[i].a);
+    c->prof.free_events.push_back(P[i].b);
+  }
+  P.erase(P.begin(), P.begin() + n);
+}
+
+void prof_end(hmc_ctx* c, int id, cudaEvent_t a) {
+  if (!c->prof.timing || a == nullptr) return;
+  if (c->prof.free_events.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->prof.free_events.push_back(e);
+  }
+  cudaEvent_t b = c->prof.free_events.back();
+  c->prof.free_events.pop_back();
+  cudaEventRecord(b, c->stream);
+  c->prof.pending.push_back(Pending{a, b, id});
+  if (c->prof.pending.size() > 16384) prof_drain(c, 8192);
+}
+
+hmc_status prepare_field(hmc_ctx* c, const double* phi) {
+  if (phi == nullptr) {
+    if (!c->field_loaded) return fail(c, HMC_ERR_INVALID, "phi is NULL and no field was loaded");
+    return HMC_OK;
+  }
+  if (((uintptr_t)phi) % 8) return fail(c, HMC_ERR_INVALID, "phi is not 8-byte aligned");
+  c->field_loaded = false;
+  return k_phase_launch(c, phi);
+}
+
+}  // namespace hmc
+
+static bool bad_lattice(const hmc_lattice* L) {
+  if (!L) return true;
+  if (L->n < 1 || L->m < 1 || L->nt < 2) return true;
+  const long long N = 2LL * L->n * L->m * L->nt;
+  if (N >= (1LL << 30)) return true;
+  if (!std::isfinite(L->kappa) || !std::isfinite(L->U) || !std::isfinite(L->beta)) return true;
+  if (!(L->beta > 0.0) || !(L->U > 0.0)) return true;
+  return false;
+}
+
+static hmc_status check_vec(hmc_ctx* c, const void* p, int prec, const char* what) {
+  if (p == nullptr) return fail(c, HMC_ERR_INVALID, std::string(what) + " is NULL");
+  const uintptr_t al = prec == 64 ? 16 : 8;
+  if (((uintptr_t)p) % al) return fail(c, HMC_ERR_INVALID, std::string(what) + " is misaligned");
+  return HMC_OK;
+}
+
+static hmc_status check_mass(hmc_ctx* c, double ms) {
+  if (!std::isfinite(ms)) return fail(c, HMC_ERR_INVALID, "staggered mass is not finite");
+  if (1.0 - c->delta * ms == 0.0) return fail(c, HMC_ERR_INVALID, "1 - delta*m_s == 0: the time hop vanishes");
+  return HMC_OK;
+}
+
+static hmc_status check_prec(hmc_ctx* c, int prec) {
+  if (prec != 32 && prec != 64) return fail(c, HMC_ERR_INVALID, "prec must be 32 or 64");
+  return HMC_OK;
+}
+
+extern "C" {
+
+int hmc_abi_version(void) { return HMC_ABI_VERSION; }
+
+const char* hmc_status_string(hmc_status s) {
+  switch (s) {
+    case HMC_OK: return "ok";
+    case HMC_ERR_INVALID: return "invalid argument";
+    case HMC_ERR_CUDA: return "CUDA error";
+    case HMC_ERR_NOT_CONVERGED: return "solver did not converge";
+    case HMC_ERR_NAN: return "NaN, Inf or breakdown in a reduction";
+    case HMC_ERR_TIMEOUT: return "device wait timed out";
+    case HMC_ERR_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* hmc_last_error(const hmc_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
+  if (!out) return HMC_ERR_INVALID;
+  *out = nullptr;
+  if (bad_lattice(lat)) return HMC_ERR_INVALID;
+  hmc_ctx* c = new hmc_ctx();
+  c->lat = *lat;
+  c->delta = lat->beta / lat->nt;
+  c->geo = make_geo(lat->n, lat->m, lat->nt, c->delta, lat->kappa);
+  c->stream = (cudaStream_t)stream;
+  auto bail = [&](cudaError_t e) {
+    cudaGetLastError();
+    hmc_destroy(c);
+    return e == cudaErrorMemoryAllocation ? HMC_ERR_NOMEM : HMC_ERR_CUDA;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(e);
+  e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(e);
+  c->max_grid = c->nsm * kMaxGridPerSM;
+  const size_t N = (size_t)c->geo.N;
+  if ((e = cudaMalloc(&c->ws[WS_E], N * sizeof(double2))) != cudaSuccess) return bail(e);
+  c->ws_bytes[WS_E] = N * sizeof(double2);
+  if ((e = cudaMalloc(&c->ws[WS_PHI32], N * sizeof(float))) != cudaSuccess) return bail(e);
+  c->ws_bytes[WS_PHI32] = N * sizeof(float);
+  if ((e = cudaMalloc(&c->partials, sizeof(double) * kMaxRed * c->max_grid)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->tickets, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemset(c->sc, 0, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->sc_host, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->dscal, sizeof(double) * 64)) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->dscal_host, sizeof(double) * 64)) != cudaSuccess) return bail(e);
+  *out = c;
+  return HMC_OK;
+}
+
+hmc_status hmc_destroy(hmc_ctx* c) {
+  if (!c) return HMC_ERR_INVALID;
+  if (c->stream || c->device >= 0) cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < WS_COUNT; ++i)
+    if (c->ws[i]) cudaFree(c->ws[i]);
+  if (c->partials) cudaFree(c->partials);
+  if (c->tickets) cudaFree(c->tickets);
+  if (c->sc) cudaFree(c->sc);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+  if (c->dscal) cudaFree(c->dscal);
+  if (c->dscal_host) cudaFreeHost(c->dscal_host);
+  for (auto& p : c->prof.pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->prof.free_events) cudaEventDestroy(e);
+  delete c;
+  return HMC_OK;
+}
+
+hmc_status hmc_set_stream(hmc_ctx* c, void* stream) {
+  if (!c) return HMC_ERR_INVALID;
+  c->stream = (cudaStream_t)stream;
+  return HMC_OK;
+}
+
+hmc_status hmc_load_field(hmc_ctx* c, const double* phi) {
+  if (!c) return HMC_ERR_INVALID;
+  if (!phi) return fail(c, HMC_ERR_INVALID, "phi is NULL");
+  HMC_TRY(prepare_field(c, phi));
+  c->field_loaded = true;
+  c->loaded_phi = phi;
+  return HMC_OK;
+}
+
+hmc_status hmc_apply_M(hmc_ctx* c, const double* phi, double ms, const void* in, void* out, int prec) {
+  if (!c) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  HMC_TRY(check_vec(c, in, prec, "in"));
+  HMC_TRY(check_vec(c, out, prec, "out"));
+  HMC_TRY(check_mass(c, ms));
+  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  HMC_TRY(prepare_field(c, phi));
+  if (prec == 64)
+    return m_launch<double>(c, c->geo, c->delta * ms, (const double2*)in, nullptr, 0.0, (double2*)out);
+  return m_launch<float>(c, c->geo, (float)(c->delta * ms), (const float2*)in, nullptr, 0.f, (float2*)out);
+}
+
+hmc_status hmc_apply_Mdag(hmc_ctx* c, const double* phi, double ms, const void* in, void* out, int prec) {
+  if (!c) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  HMC_TRY(check_vec(c, in, prec, "in"));
+  HMC_TRY(check_vec(c, out, prec, "out"));
+  HMC_TRY(check_mass(c, ms));
+  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  HMC_TRY(prepare_field(c, phi));
+  if (prec == 64) return mdag_launch<double>(c, c->geo, c->delta * ms, (const double2*)in, (double2*)out);
+  return mdag_launch<float>(c, c->geo, (float)(c->delta * ms), (const float2*)in, (float2*)out);
+}
+
+hmc_status hmc_apply_MMdag(hmc_ctx* c, const double* phi, double ms, double sigma, const void* in,
+                           void* out, int prec) {
+  if (!c) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  HMC_TRY(check_vec(c, in, prec, "in"));
+  HMC_TRY(check_vec(c, out, prec, "out"));
+  HMC_TRY(check_mass(c, ms));
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, HMC_ERR_INVALID, "sigma must be finite and >= 0");
+  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  HMC_TRY(prepare_field(c, phi));
+  const size_t N = (size_t)c->geo.N;
+  if (prec == 64) return apply_A64(c, ms, sigma, (const double2*)in, (double2*)out);
+  float2* u;
+  HMC_TRY(ws_get(c, WS_U32, sizeof(float2) * N, (void**)&u));
+  const float dm = (float)(c->delta * ms);
+  HMC_TRY(mdag_launch<float>(c, c->geo, dm, (const float2*)in, u));
+  return m_launch<float>(c, c->geo, dm, u, sigma != 0.0 ? (const float2*)in : nullptr, (float)sigma,
+                         (float2*)out);
+}
+
+static hmc_status solve_checks(hmc_ctx* c, double ms, double sigma, const void* b, void* x, int prec,
+                               double tol, int maxit) {
+  HMC_TRY(check_vec(c, b, prec, "b"));
+  HMC_TRY(check_vec(c, x, prec, "x"));
+  HMC_TRY(check_mass(c, ms));
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, HMC_ERR_INVALID, "sigma must be finite and >= 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, HMC_ERR_INVALID, "tol must be positive");
+  if (maxit < 1) return fail(c, HMC_ERR_INVALID, "maxit must be >= 1");
+  if (b == x) return fail(c, HMC_ERR_INVALID, "b and x must not overlap");
+  return HMC_OK;
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void fill_info(hmc_solve_info* info, const SolveStats& s, hmc_status st, double t0,
+                      double bytes_per_apply_site, double N) {
+  if (!info) return;
+  std::memset(info, 0, sizeof(*info));
+  info->iters = s.iters;
+  info->iters_outer = s.outer;
+  info->iters_inner = s.inner;
+  info->status = st;
+  info->true_rel_res = s.true_rel;
+  info->seconds = now_s() - t0;
+  info->applies64 = s.applies64;
+  info->applies32 = s.applies32;
+  (void)bytes_per_apply_site;
+  // algorithmic bytes: one CG iteration moves 192 B/site in FP64 and 96 B/site in FP32
+  info->bytes = (long long)(N * (192.0 * s.applies64 + 96.0 * s.applies32));
+}
+
+hmc_status hmc_solve_cg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
+                        double tol, int maxit, hmc_solve_info* info) {
+  if (!c) return HMC_ERR_INVALID;
+  const double t0 = now_s();
+  HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
+  HMC_TRY(prepare_field(c, phi));
+  SolveStats s;
+  hmc_status st = cg_core<double>(c, ms, sigma, (const double2*)b, (double2*)x, false, tol, maxit, 0, true, &s);
+  fill_info(info, s, st, t0, 0, c->geo.N);
+  return st;
+}
+
+hmc_status hmc_solve_spcg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
+                          double tol, int maxit, hmc_solve_info* info) {
+  if (!c) return HMC_ERR_INVALID;
+  const double t0 = now_s();
+  HMC_TRY(solve_checks(c, ms, sigma, b, x, 32, tol, maxit));
+  HMC_TRY(prepare_field(c, phi));
+  SolveStats s;
+  hmc_status st = cg_core<float>(c, ms, sigma, (const float2*)b, (float2*)x, true, tol, maxit, 1, true, &s);
+  fill_info(info, s, st, t0, 0, c->geo.N);
+  return st;
+}
+
+hmc_status hmc_solve_fgmres(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
+                            double tol, int restart, double a, int inner_prec, int maxit,
+                            hmc_solve_info* info) {
+  if (!c) return HMC_ERR_INVALID;
+  const double t0 = now_s();
+  HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
+  if (restart < 1 || restart > kMaxRestart) return fail(c, HMC_ERR_INVALID, "restart must be in [1, 16]");
+  if (!(a > 0.0)) return fail(c, HMC_ERR_INVALID, "a must be positive");
+  if (inner_prec != 32 && inner_prec != 64) return fail(c, HMC_ERR_INVALID, "inner_prec must be 32 or 64");
+  HMC_TRY(prepare_field(c, phi));
+  SolveStats s;
+  hmc_status st = fgmres_core(c, ms, sigma, (const double2*)b, (double2*)x, tol, restart, a, inner_prec,
+                              maxit, 1e-6, 2000, &s);
+  fill_info(info, s, st, t0, 0, c->geo.N);
+  return st;
+}
+
+hmc_status hmc_profile(hmc_ctx* c, int timing_on, int reset) {
+  if (!c) return HMC_ERR_INVALID;
+  if (reset) {
+    prof_drain(c, 0);
+    for (int i = 0; i < K_COUNT; ++i) {
+      c->prof.launches[i] = 0;
+      c->prof.ms[i] = 0.0;
+      c->prof.bytes[i] = 0.0;
+    }
+  }
+  c->prof.timing = timing_on != 0;
+  return HMC_OK;
+}
+
+hmc_status hmc_profile_read(hmc_ctx* c, hmc_kernel_stat* out, int max, int* count) {
+  if (!c || !out || !count) return HMC_ERR_INVALID;
+  prof_drain(c, 0);
+  int n = 0;
+  for (int i = 0; i < K_COUNT && n < max; ++i) {
+    std::memset(&out[n], 0, sizeof(hmc_kernel_stat));
+    std::strncpy(out[n].name, kKernelNames[i], sizeof(out[n].name) - 1);
+    out[n].launches = c->prof.launches[i];
+    out[n].ms_total = c->prof.ms[i];
+    out[n].bytes_total = c->prof.bytes[i];
+    ++n;
+  }
+  *count = n;
+  return HMC_OK;
+}
+
+}  // extern "C"

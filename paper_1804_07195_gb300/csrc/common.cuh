@@ -1,0 +1,227 @@
+// Device-side building blocks shared by the libhmc kernels: lattice geometry
+// in the canonical layout, complex arithmetic in float/double, and
+// deterministic grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hmc {
+
+// ---------------------------------------------------------------------------
+// Unsigned division by a runtime constant d >= 1 for numerators x < 2^31,
+// by multiply-high: q = (umulhi(x, mul) + x) >> shift with shift = ceil(log2 d)
+// and mul = floor(2^32 (2^shift - d) / d) + 1 (Granlund and Montgomery, 1994).
+struct FastDiv {
+  uint32_t d, mul, shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  f.shift = s;
+  f.mul = (uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1ull);
+  return f;
+}
+
+inline uint32_t fastdiv_host(uint32_t x, const FastDiv& f) {
+  uint32_t hi = (uint32_t)(((uint64_t)x * f.mul) >> 32);
+  return (hi + x) >> f.shift;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (__umulhi(x, f.mul) + x) >> f.shift;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of one n x m x nt lattice in the canonical layout
+//   idx = ((s*nt + t)*m + j)*n + i.
+// Kernels run one thread per "cell-time" q = (t*m + j)*n + i in [0, H) and
+// handle the A site q and the B site H + q together.
+struct Geo {
+  int n, m, nt;
+  int V;   // n*m cells per time slice
+  int H;   // nt*V sites per sublattice
+  int N;   // 2H
+  FastDiv fV, fn;
+  double dk;  // delta * kappa
+};
+
+inline Geo make_geo(int n, int m, int nt, double delta, double kappa) {
+  Geo g;
+  g.n = n;
+  g.m = m;
+  g.nt = nt;
+  g.V = n * m;
+  g.H = nt * g.V;
+  g.N = 2 * g.H;
+  g.fV = make_fastdiv((uint32_t)g.V);
+  g.fn = make_fastdiv((uint32_t)n);
+  g.dk = delta * kappa;
+  return g;
+}
+
+// Indices of everything a thread at cell-time q touches.
+struct Nbr {
+  int q;             // A(i,j,t); B(i,j,t) is H + q
+  int tm, tp;        // same cell at t-1, t+1 (wrapped), within a sublattice half
+  int im1, jm1;      // A-row partners: cells (i-1,j), (i,j-1) at t
+  int ip1, jp1;      // B-row partners: cells (i+1,j), (i,j+1) at t
+  bool wrap_tm;      // t == 0: the t-1 hop wraps (anti-periodic: sign -1)
+  bool wrap_tp;      // t == nt-1: the t+1 hop wraps
+};
+
+__device__ __forceinline__ Nbr neighbours(const Geo& g, int q) {
+  Nbr b;
+  b.q = q;
+  int t = (int)fdiv((uint32_t)q, g.fV);
+  int c = q - t * g.V;
+  int j = (int)fdiv((uint32_t)c, g.fn);
+  int i = c - j * g.n;
+  b.wrap_tm = (t == 0);
+  b.wrap_tp = (t == g.nt - 1);
+  b.tm = q - g.V + (b.wrap_tm ? g.H : 0);
+  b.tp = q + g.V - (b.wrap_tp ? g.H : 0);
+  b.im1 = q - 1 + (i == 0 ? g.n : 0);
+  b.jm1 = q - g.n + (j == 0 ? g.V : 0);
+  b.ip1 = q + 1 - (i == g.n - 1 ? g.n : 0);
+  b.jp1 = q + g.n - (j == g.m - 1 ? g.V : 0);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Complex values in the compute precision R (float or double).
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> ld(const float2* p, int k) {
+  float2 v = p[k];
+  return Cx<R>{(R)v.x, (R)v.y};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> ld(const double2* p, int k) {
+  double2 v = p[k];
+  return Cx<R>{(R)v.x, (R)v.y};
+}
+__device__ __forceinline__ void st(float2* p, int k, Cx<float> v) { p[k] = make_float2(v.re, v.im); }
+__device__ __forceinline__ void st(float2* p, int k, Cx<double> v) {
+  p[k] = make_float2((float)v.re, (float)v.im);
+}
+__device__ __forceinline__ void st(double2* p, int k, Cx<double> v) { p[k] = make_double2(v.re, v.im); }
+__device__ __forceinline__ void st(double2* p, int k, Cx<float> v) {
+  p[k] = make_double2((double)v.re, (double)v.im);
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cneg_if(Cx<R> a, bool neg) {
+  return neg ? Cx<R>{-a.re, -a.im} : a;
+}
+
+template <typename R>
+__device__ __forceinline__ R norm2(Cx<R> a) {
+  return a.re * a.re + a.im * a.im;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reductions.
+//
+// Every block reduces its threads' values in a fixed shuffle/shared-memory
+// order and writes one partial per value to partials[v * gridDim.x + block].
+// The last block to arrive (atomic ticket) sums the partials of every value in
+// a fixed order and hands the totals to a finisher run by its thread 0. The
+// result therefore does not depend on block scheduling.
+constexpr int kMaxBlockThreads = 256;
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* K * 32 */) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) smem[k * 32 + warp] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = lane < nw ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Returns true in the last block after the totals were written to `tot` (valid
+// in thread 0 of that block only).
+template <int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* ticket,
+                                         double (&tot)[K]) {
+  __shared__ double smem[K * 32];
+  __shared__ bool am_last;
+  block_sum<K>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      acc += __ldcg(&partials[k * gridDim.x + b]);
+    w[k] = acc;
+  }
+  block_sum<K>(w, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = w[k];
+    *ticket = 0u;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Device-side scalar state of one CG solve (shared by the FP64 and FP32 paths).
+struct CGScal {
+  double rr;     // |r|^2 of the current residual
+  double pAp;    // <p, A p>
+  double alpha, beta;
+  double bb;     // |b|^2
+  double thresh; // stop when rr <= thresh (= tol^2 |b|^2)
+  double sigma;  // shift of the operator
+  int iter, maxit;
+  int done;      // 0 running, 1 converged, 2 iteration limit, 3 breakdown (pAp <= 0 / NaN)
+  int pad;
+};
+
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+
+}  // namespace hmc

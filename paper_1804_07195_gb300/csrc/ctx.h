@@ -1,0 +1,170 @@
+// Internal definition of the library context: stream, geometry, phase tables,
+// workspace pool, reduction scratch and launch instrumentation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "hmc.h"
+
+namespace hmc {
+
+// Kernel identifiers for the launch counters and event timing.
+enum KernelId {
+  K_PHASE = 0,
+  K_MDAG64,
+  K_M64,
+  K_MDAG32,
+  K_M32,
+  K_CG_MDAG64,
+  K_CG_M64,
+  K_CG_P64,
+  K_CG_MDAG32,
+  K_CG_M32,
+  K_CG_P32,
+  K_RESID64,
+  K_RESID32,
+  K_INIT0,
+  K_CONVERT,
+  K_NORM,
+  K_MDOT,
+  K_GSUPD,
+  K_SCALE,
+  K_XUPD,
+  K_FORCE,
+  K_AXPY,
+  K_MD,
+  K_BATCH_MDAG,
+  K_BATCH_M,
+  K_BATCH_P,
+  K_BATCH_RESID,
+  K_BATCH_MISC,
+  K_COUNT
+};
+
+extern const char* const kKernelNames[K_COUNT];
+extern const double kKernelBytesPerSite[K_COUNT];
+
+// Named workspace slots owned by the context.
+enum WsSlot {
+  WS_E = 0,      // e^{i phi} table, complex128
+  WS_PHI32,      // phi rounded to float
+  WS_U64,        // M^dagger intermediate, complex128
+  WS_U32,
+  WS_CG_R64, WS_CG_P64, WS_CG_X64,
+  WS_CG_R32, WS_CG_P32, WS_CG_X32, WS_CG_B32,
+  WS_FG_R, WS_FG_W, WS_FG_X, WS_FG_V, WS_FG_Z,  // FGMRES vectors; V, Z hold `restart` each
+  WS_F_ETA, WS_F_XI, WS_F_SRC, WS_F_TMP,        // force / action temporaries
+  WS_MD_CHI, WS_MD_GRAD, WS_MD_FORCE,           // trajectory: pseudofermions, level forces
+  WS_MD_PHI0,
+  WS_BATCH,
+  WS_COUNT
+};
+
+struct Pending {
+  cudaEvent_t a, b;
+  int id;
+};
+
+struct ProfileState {
+  bool timing = false;
+  long long launches[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  double bytes[K_COUNT] = {};  // algorithmic bytes summed over launches
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+};
+
+}  // namespace hmc
+
+struct hmc_ctx {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  hmc_lattice lat{};
+  hmc::Geo geo{};
+  double delta = 0.0;
+  std::string err;
+
+  bool field_loaded = false;  // E / phi32 hold the field given to hmc_load_field
+  const double* loaded_phi = nullptr;
+
+  void* ws[hmc::WS_COUNT] = {};
+  size_t ws_bytes[hmc::WS_COUNT] = {};
+
+  double* partials = nullptr;      // reduction partials, kPartials doubles
+  unsigned int* tickets = nullptr; // one ticket per concurrent reduction site
+  hmc::CGScal* sc = nullptr;       // device CG state (two: FP64 outer, FP32 inner)
+  hmc::CGScal* sc_host = nullptr;  // pinned mirror
+  double* dscal = nullptr;         // device scalar results (64 doubles)
+  double* dscal_host = nullptr;    // pinned mirror
+  int max_grid = 0;
+
+  hmc::ProfileState prof;
+};
+
+namespace hmc {
+
+constexpr int kThreads = 256;
+constexpr int kMaxGridPerSM = 8;
+constexpr int kMaxRed = 40;  // values reduced at once at most
+constexpr int kTickets = 16;
+
+// Record an error message on ctx and return the status.
+hmc_status fail(hmc_ctx* c, hmc_status s, const std::string& msg);
+// Turn a CUDA error into HMC_ERR_CUDA with a message.
+hmc_status cuda_fail(hmc_ctx* c, cudaError_t e, const char* what);
+
+#define HMC_CUDA(ctx, call)                                        \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return hmc::cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+#define HMC_TRY(expr)                  \
+  do {                                 \
+    hmc_status s_ = (expr);            \
+    if (s_ != HMC_OK) return s_;       \
+  } while (0)
+
+// Workspace slot of at least `bytes` bytes (grown on demand, never shrunk).
+hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out);
+
+// Grid size for a grid-stride kernel over `work` threads.
+inline int grid_for(const hmc_ctx* c, long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  if (g > c->max_grid) g = c->max_grid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Instrumented launch: counts, and brackets with events when timing is on.
+void prof_begin(hmc_ctx* c, int id, cudaEvent_t* a);
+void prof_end(hmc_ctx* c, int id, cudaEvent_t a);
+
+// `bytes`: algorithmic bytes of this launch; negative = the kernel's bytes per
+// site times the context's site count.
+template <typename F>
+inline hmc_status launch_b(hmc_ctx* c, int id, double bytes, F&& f) {
+  cudaEvent_t a = nullptr;
+  c->prof.bytes[id] += bytes >= 0 ? bytes : kKernelBytesPerSite[id] * (double)c->geo.N;
+  prof_begin(c, id, &a);
+  f();
+  prof_end(c, id, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, kKernelNames[id]);
+  return HMC_OK;
+}
+
+template <typename F>
+inline hmc_status launch(hmc_ctx* c, int id, F&& f) {
+  return launch_b(c, id, -1.0, f);
+}
+
+// Build the phase tables of phi (or reuse the loaded field when phi is NULL).
+hmc_status prepare_field(hmc_ctx* c, const double* phi);
+
+}  // namespace hmc

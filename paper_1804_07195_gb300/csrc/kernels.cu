@@ -1,0 +1,585 @@
+// The libhmc kernels: operator applications, fused CG iterations, residuals,
+// FGMRES vector operations and the pseudofermion force.
+#include "kernels.h"
+#include "operator.cuh"
+
+namespace hmc {
+
+// Algorithmic HBM bytes per lattice site of each kernel (reads + writes of the
+// arrays it must touch, each once), used to report achieved bandwidth.
+const char* const kKernelNames[K_COUNT] = {
+    "phase_table",    "apply_Mdag_f64", "apply_M_f64",   "apply_Mdag_f32", "apply_M_f32",
+    "cg_Mdag_f64",    "cg_M_update_f64", "cg_p_f64",     "cg_Mdag_f32",    "cg_M_update_f32",
+    "cg_p_f32",       "residual_f64",   "residual_f32",  "cg_init0",       "convert",
+    "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
+    "force",          "axpy",           "md_update",     "batch_Mdag",     "batch_M_update",
+    "batch_p",        "batch_residual", "batch_misc"};
+
+const double kKernelBytesPerSite[K_COUNT] = {
+    8 + 16 + 4,          // phase: phi in, E and phi32 out
+    16 + 16 + 16,        // M^dagger f64: in, E, out
+    16 + 16 + 16,        // M f64
+    8 + 4 + 8,           // M^dagger f32: in, phi32, out
+    8 + 4 + 8,           // M f32
+    16 + 16 + 16,        // cg M^dagger f64: p, E, u
+    16 + 16 + 16 + 32 + 32,  // cg M f64: u, E, p, x rw, r rw
+    16 + 32,             // p = r + beta p
+    8 + 4 + 8,           // cg M^dagger f32
+    8 + 4 + 8 + 16 + 16, // cg M f32
+    8 + 16,              // p f32
+    16 + 16 + 16 + 16 + 16,  // residual f64: u, E, x, b, r
+    8 + 4 + 8 + 8 + 8,   // residual f32
+    16 + 16 * 3,         // init0 (f64 sizes)
+    16 + 8,              // convert
+    16,                  // norm2
+    0,                   // mdot (depends on the basis size)
+    0,                   // gs update
+    16 + 16 + 8,         // scale
+    0,                   // x update
+    16 + 16 + 16 + 16 + 16,  // force: eta, E, xi, chi, grad rw
+    24,                  // axpy
+    24,                  // md update
+    16 + 16 + 16, 16 + 16 + 16 + 32 + 32, 16 + 32, 16 * 5, 0};
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restrict__ phi,
+                                                    double2* __restrict__ E,
+                                                    float* __restrict__ phi32) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double s, co;
+    double x = phi[k];
+    sincos(x, &s, &co);
+    E[k] = make_double2(co, s);
+    phi32[k] = (float)x;
+  }
+}
+
+template <typename R>
+Phase<R> phase_of(hmc_ctx* c);
+template <>
+Phase<double> phase_of<double>(hmc_ctx* c) {
+  return Phase<double>{(const double2*)c->ws[WS_E]};
+}
+template <>
+Phase<float> phase_of<float>(hmc_ctx* c) {
+  return Phase<float>{(const float*)c->ws[WS_PHI32]};
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_mdag(Geo g, Phase<R> ph, R dm,
+                                                   const V2<R>* __restrict__ p,
+                                                   V2<R>* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = mdag_pair<R>(g, ph, dm, p, nb);
+    st(out, q, o.a);
+    st(out, g.H + q, o.b);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_m(Geo g, Phase<R> ph, R dm, const V2<R>* __restrict__ u,
+                                                const V2<R>* __restrict__ y, R sigma,
+                                                V2<R>* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = m_pair<R>(g, ph, dm, u, nb);
+    if (y != nullptr) {
+      Cx<R> ya = ld<R>(y, q), yb = ld<R>(y, g.H + q);
+      o.a.re = fma(sigma, ya.re, o.a.re);
+      o.a.im = fma(sigma, ya.im, o.a.im);
+      o.b.re = fma(sigma, yb.re, o.b.re);
+      o.b.im = fma(sigma, yb.im, o.b.im);
+    }
+    st(out, q, o.a);
+    st(out, g.H + q, o.b);
+  }
+}
+
+// u = M^dagger p; pAp = |u|^2 + sigma |p|^2 = <p, (M M^dagger + sigma) p>; alpha = rr / pAp.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_cg_mdag(Geo g, Phase<R> ph, R dm,
+                                                      const V2<R>* __restrict__ p,
+                                                      V2<R>* __restrict__ u, CGScal* sc,
+                                                      double* partials, unsigned* ticket) {
+  if (sc->done) return;
+  const R sigma = (R)sc->sigma;
+  double acc[1] = {0.0};
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = mdag_pair<R>(g, ph, dm, p, nb);
+    st(u, q, o.a);
+    st(u, g.H + q, o.b);
+    R loc = norm2(o.a) + norm2(o.b);
+    if (sigma != (R)0) loc += sigma * (norm2(ld<R>(p, q)) + norm2(ld<R>(p, g.H + q)));
+    acc[0] += (double)loc;
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    sc->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      sc->alpha = 0.0;
+      sc->done = CG_BREAKDOWN;
+    } else {
+      sc->alpha = sc->rr / pAp;
+    }
+  }
+}
+
+// A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_cg_m(Geo g, Phase<R> ph, R dm,
+                                                   const V2<R>* __restrict__ u,
+                                                   const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
+                                                   V2<R>* __restrict__ r, CGScal* sc,
+                                                   double* partials, unsigned* ticket) {
+  if (sc->done) return;
+  const R sigma = (R)sc->sigma;
+  const R alpha = (R)sc->alpha;
+  double acc[1] = {0.0};
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = m_pair<R>(g, ph, dm, u, nb);
+    R loc = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = h ? g.H + q : q;
+      Cx<R> Ap = h ? o.b : o.a;
+      Cx<R> pk = ld<R>(p, k), xk = ld<R>(x, k), rk = ld<R>(r, k);
+      Ap.re = fma(sigma, pk.re, Ap.re);
+      Ap.im = fma(sigma, pk.im, Ap.im);
+      xk.re = fma(alpha, pk.re, xk.re);
+      xk.im = fma(alpha, pk.im, xk.im);
+      rk.re = fma(-alpha, Ap.re, rk.re);
+      rk.im = fma(-alpha, Ap.im, rk.im);
+      st(x, k, xk);
+      st(r, k, rk);
+      loc += norm2(rk);
+    }
+    acc[0] += (double)loc;
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    double rr = tot[0];
+    sc->beta = rr / sc->rr;
+    sc->rr = rr;
+    sc->iter += 1;
+    if (!isfinite(rr))
+      sc->done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      sc->done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      sc->done = CG_MAXIT;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_cg_p(int N, const V2<R>* __restrict__ r,
+                                                   V2<R>* __restrict__ p, const CGScal* sc) {
+  if (sc->done) return;
+  const R beta = (R)sc->beta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    Cx<R> rk = ld<R>(r, k), pk = ld<R>(p, k);
+    pk.re = fma(beta, pk.re, rk.re);
+    pk.im = fma(beta, pk.im, rk.im);
+    st(p, k, pk);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
+                                                    const V2<R>* __restrict__ u,
+                                                    const V2<R>* __restrict__ x,
+                                                    const V2<R>* __restrict__ b, R sigma,
+                                                    V2<R>* __restrict__ r, V2<R>* __restrict__ p,
+                                                    CGScal* init, double tol2, int maxit,
+                                                    double dsigma, double* out2, double* partials,
+                                                    unsigned* ticket) {
+  double acc[2] = {0.0, 0.0};
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = m_pair<R>(g, ph, dm, u, nb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = h ? g.H + q : q;
+      Cx<R> Ax = h ? o.b : o.a;
+      Cx<R> xk = ld<R>(x, k), bk = ld<R>(b, k);
+      Cx<R> rk;
+      rk.re = bk.re - fma(sigma, xk.re, Ax.re);
+      rk.im = bk.im - fma(sigma, xk.im, Ax.im);
+      st(r, k, rk);
+      if (p != nullptr) st(p, k, rk);
+      acc[0] += (double)norm2(rk);
+      acc[1] += (double)norm2(bk);
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    if (out2 != nullptr) {
+      out2[0] = tot[0];
+      out2[1] = tot[1];
+    }
+    if (init != nullptr) {
+      init->rr = tot[0];
+      init->bb = tot[1];
+      init->thresh = tol2 * tot[1];
+      init->sigma = dsigma;
+      init->iter = 0;
+      init->maxit = maxit;
+      init->alpha = init->beta = init->pAp = 0.0;
+      init->done = (tot[0] <= init->thresh) ? CG_CONVERGED : CG_RUNNING;
+      if (!isfinite(tot[0])) init->done = CG_BREAKDOWN;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restrict__ b,
+                                                    V2<R>* __restrict__ x, V2<R>* __restrict__ r,
+                                                    V2<R>* __restrict__ p, CGScal* sc, double tol2,
+                                                    int maxit, double sigma, double* partials,
+                                                    unsigned* ticket) {
+  double acc[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    Cx<R> bk = ld<R>(b, k);
+    st(x, k, Cx<R>{(R)0, (R)0});
+    st(r, k, bk);
+    st(p, k, bk);
+    acc[0] += (double)norm2(bk);
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    sc->rr = tot[0];
+    sc->bb = tot[0];
+    sc->thresh = tol2 * tot[0];
+    sc->sigma = sigma;
+    sc->iter = 0;
+    sc->maxit = maxit;
+    sc->alpha = sc->beta = sc->pAp = 0.0;
+    sc->done = (tot[0] <= sc->thresh) ? CG_CONVERGED : CG_RUNNING;
+    if (!isfinite(tot[0])) sc->done = CG_BREAKDOWN;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_to32(int N, const double2* __restrict__ in,
+                                                   float2* __restrict__ out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 v = in[k];
+    out[k] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_to64(int N, const float2* __restrict__ in,
+                                                   double2* __restrict__ out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    float2 v = in[k];
+    out[k] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_norm2(int N, const double2* __restrict__ v, double* out,
+                                                    double* partials, unsigned* ticket) {
+  double acc[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 a = v[k];
+    acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_redot(int N, const double2* __restrict__ u,
+                                                    const double2* __restrict__ v, double* out,
+                                                    double* partials, unsigned* ticket) {
+  double acc[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 a = u[k], b = v[k];
+    acc[0] = fma(a.x, b.x, fma(a.y, b.y, acc[0]));
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+// h[i] = V_i^H w for i < NV (compile-time upper bound on nv).
+template <int NV>
+__global__ void __launch_bounds__(kThreads) k_mdot(int N, VecList V, int nv,
+                                                   const double2* __restrict__ w, double* hout,
+                                                   double* partials, unsigned* ticket) {
+  double acc[2 * NV];
+#pragma unroll
+  for (int i = 0; i < 2 * NV; ++i) acc[i] = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 wk = w[k];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < nv) {
+        double2 vk = V.v[i][k];
+        // conj(v) w
+        acc[2 * i] = fma(vk.x, wk.x, fma(vk.y, wk.y, acc[2 * i]));
+        acc[2 * i + 1] = fma(vk.x, wk.y, fma(-vk.y, wk.x, acc[2 * i + 1]));
+      }
+    }
+  }
+  double tot[2 * NV];
+  if (grid_sum<2 * NV>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    for (int i = 0; i < 2 * nv; ++i) hout[i] = tot[i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gsupd(int N, VecList V, int nv, const double* h,
+                                                    double2* __restrict__ w, double* ww,
+                                                    double* partials, unsigned* ticket) {
+  __shared__ double hs[2 * kMaxRestart];
+  if (threadIdx.x < 2 * nv) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 wk = w[k];
+    for (int i = 0; i < nv; ++i) {
+      double2 vk = V.v[i][k];
+      const double hr = hs[2 * i], hi = hs[2 * i + 1];
+      // w -= h v
+      wk.x = fma(-hr, vk.x, fma(hi, vk.y, wk.x));
+      wk.y = fma(-hr, vk.y, fma(-hi, vk.x, wk.y));
+    }
+    w[k] = wk;
+    acc[0] = fma(wk.x, wk.x, fma(wk.y, wk.y, acc[0]));
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *ww = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_scale(int N, double s, const double2* __restrict__ w,
+                                                    double2* __restrict__ v, float2* __restrict__ v32) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 a = w[k];
+    a.x *= s;
+    a.y *= s;
+    v[k] = a;
+    if (v32 != nullptr) v32[k] = make_float2((float)a.x, (float)a.y);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_xupd(int N, VecList Z, CoefList y, int nz,
+                                                   double2* __restrict__ x) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 xk = x[k];
+    for (int i = 0; i < nz; ++i) {
+      double2 z = Z.v[i][k];
+      xk.x = fma(y.re[i], z.x, fma(-y.im[i], z.y, xk.x));
+      xk.y = fma(y.re[i], z.y, fma(y.im[i], z.x, xk.y));
+    }
+    x[k] = xk;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_axpy_real(int N, double a, const double* __restrict__ x,
+                                                        double* __restrict__ y) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
+    y[k] = fma(a, x[k], y[k]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_axpby_c(int N, double a, const double2* __restrict__ x,
+                                                      double b, double2* __restrict__ y) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double2 xv = x[k], yv = y[k];
+    y[k] = make_double2(fma(a, xv.x, b * yv.x), fma(a, xv.y, b * yv.y));
+  }
+}
+
+// Force of one term at the cell-time q. dM/dphi in row k is i s e^{+i phi} (A)
+// or i s e^{-i phi} (B), s = -1 on the wrapping hop; its column is the time
+// partner (t-1 for A, t+1 for B). With c = conj(eta_k) dM_k w_tp:
+//   -2 Re(c) = 2 s Im(conj(eta) e^{+-i phi} w_tp).
+__global__ void __launch_bounds__(kThreads) k_force(Geo g, Phase<double> ph,
+                                                    const double2* __restrict__ eta,
+                                                    const double2* __restrict__ xi,
+                                                    const double2* __restrict__ chi,
+                                                    double* __restrict__ grad) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = h ? g.H + q : q;
+      const int kp = h ? g.H + nb.tp : nb.tm;
+      const bool wrap = h ? nb.wrap_tp : nb.wrap_tm;
+      Cx<double> e = ph(k);
+      if (h) e.im = -e.im;  // B rows: e^{-i phi}
+      double2 wv = xi[kp];
+      if (chi != nullptr) {
+        double2 cv = chi[kp];
+        wv.x -= cv.x;
+        wv.y -= cv.y;
+      }
+      double2 et = eta[k];
+      // c0 = e * w ;  Im(conj(eta) c0) = et.x * c0.im - et.y * c0.re
+      double c0r = e.re * wv.x - e.im * wv.y;
+      double c0i = e.re * wv.y + e.im * wv.x;
+      double im = et.x * c0i - et.y * c0r;
+      double val = 2.0 * (wrap ? -im : im);
+      grad[k] += val;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gauss_grad(int N, const double* __restrict__ phi,
+                                                         double inv_dU, int accumulate,
+                                                         double* __restrict__ grad) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double v = phi[k] * inv_dU;
+    grad[k] = accumulate ? grad[k] + v : v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __restrict__ a, double sa,
+                                                      const double* __restrict__ b, double* out,
+                                                      double* partials, unsigned* ticket) {
+  double acc[2] = {0.0, 0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double x = a[k];
+    acc[0] = fma(x, x, acc[0]);
+    if (b != nullptr) {
+      double y = b[k];
+      acc[1] = fma(y, y, acc[1]);
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    out[0] = 0.5 * sa * tot[0];
+    out[1] = 0.5 * tot[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+#define GRID(work) grid_for(c, (work)), kThreads, 0, c->stream
+
+hmc_status k_phase_launch(hmc_ctx* c, const double* phi) {
+  const int N = c->geo.N;
+  return launch(c, K_PHASE, [&] {
+    k_phase<<<GRID(N)>>>(N, phi, (double2*)c->ws[WS_E], (float*)c->ws[WS_PHI32]);
+  });
+}
+
+template <typename R>
+hmc_status mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* out) {
+  return launch(c, sizeof(R) == 8 ? K_MDAG64 : K_MDAG32,
+                [&] { k_mdag<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, p, out); });
+}
+template <typename R>
+hmc_status m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* y, R sigma,
+                    V2<R>* out) {
+  return launch(c, sizeof(R) == 8 ? K_M64 : K_M32,
+                [&] { k_m<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, y, sigma, out); });
+}
+template <typename R>
+hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* u, CGScal* sc,
+                          unsigned* ticket) {
+  return launch(c, sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, [&] {
+    k_cg_mdag<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, p, u, sc, c->partials, ticket);
+  });
+}
+template <typename R>
+hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* p, V2<R>* x,
+                       V2<R>* r, CGScal* sc, unsigned* ticket) {
+  return launch(c, sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, [&] {
+    k_cg_m<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, p, x, r, sc, c->partials, ticket);
+  });
+}
+template <typename R>
+hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc) {
+  return launch(c, sizeof(R) == 8 ? K_CG_P64 : K_CG_P32,
+                [&] { k_cg_p<R><<<GRID(N)>>>(N, r, p, sc); });
+}
+template <typename R>
+hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
+                        const V2<R>* b, double sigma, V2<R>* r, V2<R>* p, CGScal* init,
+                        double tol2, int maxit, double* out2, unsigned* ticket) {
+  return launch(c, sizeof(R) == 8 ? K_RESID64 : K_RESID32, [&] {
+    k_resid<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, x, b, (R)sigma, r, p, init, tol2, maxit,
+                              sigma, out2, c->partials, ticket);
+  });
+}
+template <typename R>
+hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V2<R>* p, CGScal* sc,
+                        double tol2, int maxit, double sigma, unsigned* ticket) {
+  return launch(c, K_INIT0, [&] {
+    k_init0<R><<<GRID(N)>>>(N, b, x, r, p, sc, tol2, maxit, sigma, c->partials, ticket);
+  });
+}
+
+#define INST(R)                                                                                   \
+  template hmc_status mdag_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, V2<R>*);             \
+  template hmc_status m_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*, R,        \
+                                  V2<R>*);                                                        \
+  template hmc_status cg_mdag_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, V2<R>*, CGScal*,  \
+                                        unsigned*);                                               \
+  template hmc_status cg_m_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*,        \
+                                     V2<R>*, V2<R>*, CGScal*, unsigned*);                         \
+  template hmc_status cg_p_launch<R>(hmc_ctx*, int, const V2<R>*, V2<R>*, const CGScal*);        \
+  template hmc_status resid_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*,       \
+                                      const V2<R>*, double, V2<R>*, V2<R>*, CGScal*, double, int, \
+                                      double*, unsigned*);                                        \
+  template hmc_status init0_launch<R>(hmc_ctx*, int, const V2<R>*, V2<R>*, V2<R>*, V2<R>*,       \
+                                      CGScal*, double, int, double, unsigned*);
+INST(float)
+INST(double)
+#undef INST
+
+hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out) {
+  return launch(c, K_CONVERT, [&] { k_to32<<<GRID(N)>>>(N, in, out); });
+}
+hmc_status to64_launch(hmc_ctx* c, int N, const float2* in, double2* out) {
+  return launch(c, K_CONVERT, [&] { k_to64<<<GRID(N)>>>(N, in, out); });
+}
+hmc_status norm2_launch(hmc_ctx* c, int N, const double2* v, double* out, unsigned* ticket) {
+  return launch(c, K_NORM, [&] { k_norm2<<<GRID(N)>>>(N, v, out, c->partials, ticket); });
+}
+hmc_status redot_launch(hmc_ctx* c, int N, const double2* u, const double2* v, double* out,
+                        unsigned* ticket) {
+  return launch(c, K_NORM, [&] { k_redot<<<GRID(N)>>>(N, u, v, out, c->partials, ticket); });
+}
+hmc_status mdot_launch(hmc_ctx* c, int N, VecList V, int nv, const double2* w, double* hout,
+                       unsigned* ticket) {
+  return launch_b(c, K_MDOT, 16.0 * N * (nv + 1), [&] {
+    if (nv <= 4)
+      k_mdot<4><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
+    else if (nv <= 8)
+      k_mdot<8><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
+    else
+      k_mdot<kMaxRestart><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
+  });
+}
+hmc_status gsupd_launch(hmc_ctx* c, int N, VecList V, int nv, const double* h, double2* w,
+                        double* ww, unsigned* ticket) {
+  return launch_b(c, K_GSUPD, 16.0 * N * (nv + 2),
+                [&] { k_gsupd<<<GRID(N)>>>(N, V, nv, h, w, ww, c->partials, ticket); });
+}
+hmc_status scale_launch(hmc_ctx* c, int N, double s, const double2* w, double2* v, float2* v32) {
+  return launch(c, K_SCALE, [&] { k_scale<<<GRID(N)>>>(N, s, w, v, v32); });
+}
+hmc_status xupd_launch(hmc_ctx* c, int N, VecList Z, CoefList y, int nz, double2* x) {
+  return launch_b(c, K_XUPD, 16.0 * N * (nz + 2), [&] { k_xupd<<<GRID(N)>>>(N, Z, y, nz, x); });
+}
+hmc_status axpy_real_launch(hmc_ctx* c, int N, double a, const double* x, double* y) {
+  return launch(c, K_AXPY, [&] { k_axpy_real<<<GRID(N)>>>(N, a, x, y); });
+}
+hmc_status axpby_c_launch(hmc_ctx* c, int N, double a, const double2* x, double b, double2* y) {
+  return launch(c, K_AXPY, [&] { k_axpby_c<<<GRID(N)>>>(N, a, x, b, y); });
+}
+hmc_status force_launch(hmc_ctx* c, const Geo& g, const double2* eta, const double2* xi,
+                        const double2* chi, double* grad) {
+  return launch(c, K_FORCE,
+                [&] { k_force<<<GRID(g.H)>>>(g, phase_of<double>(c), eta, xi, chi, grad); });
+}
+hmc_status gauss_grad_launch(hmc_ctx* c, int N, const double* phi, double inv_dU, int accumulate,
+                             double* grad) {
+  return launch(c, K_MD, [&] { k_gauss_grad<<<GRID(N)>>>(N, phi, inv_dU, accumulate, grad); });
+}
+hmc_status half_sq_launch(hmc_ctx* c, int N, const double* a, double sa, const double* b, double* out,
+                          unsigned* ticket) {
+  return launch(c, K_NORM,
+                [&] { k_half_sq<<<GRID(N)>>>(N, a, sa, b, out, c->partials, ticket); });
+}
+
+}  // namespace hmc

@@ -1,0 +1,89 @@
+// Host-side launchers of the libhmc kernels (kernels.cu). Every launcher
+// enqueues on ctx->stream and returns a status; none synchronises.
+#pragma once
+
+#include "ctx.h"
+
+namespace hmc {
+
+template <typename R>
+using V2 = typename Vec2<R>::type;
+
+// Phase tables: E = e^{i phi} (complex128) and phi rounded to float.
+hmc_status k_phase_launch(hmc_ctx* c, const double* phi);
+
+// out = M^dagger p, out = M u + sigma y (y may be NULL).
+template <typename R>
+hmc_status mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* out);
+template <typename R>
+hmc_status m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* y, R sigma,
+                    V2<R>* out);
+
+// CG building blocks on the state sc (see common.cuh).
+template <typename R>
+hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* u, CGScal* sc,
+                          unsigned* ticket);
+template <typename R>
+hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* p, V2<R>* x,
+                       V2<R>* r, CGScal* sc, unsigned* ticket);
+template <typename R>
+hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc);
+
+// r = b - (M u + sigma x), with |r|^2 and |b|^2 reduced. When init != NULL the
+// last block initialises a CG state (rr, bb, thresh = tol2 * bb, iter 0, done if
+// rr <= thresh) and p = r is written. When out2 != NULL it receives {|r|^2, |b|^2}.
+template <typename R>
+hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
+                        const V2<R>* b, double sigma, V2<R>* r, V2<R>* p, CGScal* init,
+                        double tol2, int maxit, double* out2, unsigned* ticket);
+
+// x = 0, r = p = b, |b|^2 reduced into a fresh CG state.
+template <typename R>
+hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V2<R>* p, CGScal* sc,
+                        double tol2, int maxit, double sigma, unsigned* ticket);
+
+// Precision conversions.
+hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out);
+hmc_status to64_launch(hmc_ctx* c, int N, const float2* in, double2* out);
+
+// |v|^2 into *out (device).
+hmc_status norm2_launch(hmc_ctx* c, int N, const double2* v, double* out, unsigned* ticket);
+
+// FGMRES pieces (Algorithm A.1), all FP64:
+//   mdot:  h[i] = V_i^H w, i < nv (complex, written to hout as 2*nv doubles)
+//   gsupd: w -= sum_i h[i] V_i, then |w|^2 into *ww
+//   scale: v = s w and v32 = (float) v
+//   xupd:  x += sum_i y[i] Z_i
+constexpr int kMaxRestart = 16;
+struct VecList {
+  const double2* v[kMaxRestart];
+};
+struct CoefList {
+  double re[kMaxRestart], im[kMaxRestart];
+};
+hmc_status mdot_launch(hmc_ctx* c, int N, VecList V, int nv, const double2* w, double* hout,
+                       unsigned* ticket);
+hmc_status gsupd_launch(hmc_ctx* c, int N, VecList V, int nv, const double* h, double2* w,
+                        double* ww, unsigned* ticket);
+hmc_status scale_launch(hmc_ctx* c, int N, double s, const double2* w, double2* v, float2* v32);
+hmc_status xupd_launch(hmc_ctx* c, int N, VecList Z, CoefList y, int nz, double2* x);
+
+// y = a x + y (real vectors) and y = a x + b y (complex128).
+hmc_status axpy_real_launch(hmc_ctx* c, int N, double a, const double* x, double* y);
+hmc_status axpby_c_launch(hmc_ctx* c, int N, double a, const double2* x, double b, double2* y);
+
+// Force of one pseudofermion term (Eqs. f_chi_i / p_dot), accumulated:
+//   g[k] += -2 Re( conj(eta[k]) dM_k w[tp(k)] ),  w = xi - chi (chi may be NULL).
+hmc_status force_launch(hmc_ctx* c, const Geo& g, const double2* eta, const double2* xi,
+                        const double2* chi, double* grad);
+// g[k] (+)= phi[k] / (delta U)
+hmc_status gauss_grad_launch(hmc_ctx* c, int N, const double* phi, double inv_dU, int accumulate,
+                             double* grad);
+// *out = sum phi^2 / 2 * scale_phi + sum pi^2 / 2 (pi may be NULL), deterministic.
+hmc_status half_sq_launch(hmc_ctx* c, int N, const double* a, double sa, const double* b, double* out,
+                          unsigned* ticket);
+// *out = Re(u^H v) (deterministic)
+hmc_status redot_launch(hmc_ctx* c, int N, const double2* u, const double2* v, double* out,
+                        unsigned* ticket);
+
+}  // namespace hmc

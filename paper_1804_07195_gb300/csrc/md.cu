@@ -1,0 +1,265 @@
+// One HMC molecular-dynamics trajectory on the device (Section 2's HMC outline,
+// Section 4's integrators, Section 5.2's nested time scales).
+//
+//   Q(c):     phi <- phi + c pi
+//   P(k, c):  pi  <- pi - c dS_k/dphi(phi)
+// Level k < n is the chi_k Hasenbusch term, level n the Gaussian term plus
+// chi_n. Each level keeps its last force with the field version it was
+// computed at, so a force is evaluated once per distinct field; momentum
+// updates are never merged.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "force.h"
+
+namespace hmc {
+
+struct MD {
+  hmc_ctx* c;
+  double* phi;
+  double* pi;
+  int nmass;
+  const double* masses;
+  const double2* const* chi;
+  const hmc_solver_opts* o;
+  double* cache;   // (nmass + 1) x N forces
+  std::vector<long long> cache_ver;
+  long long ver = 0;
+  long long tables_ver = -1;
+  SolveStats st;
+  int nforce = 0;
+  hmc_status err = HMC_OK;
+
+  size_t N() const { return (size_t)c->geo.N; }
+
+  hmc_status tables() {
+    if (tables_ver == ver) return HMC_OK;
+    HMC_TRY(prepare_field(c, phi));
+    tables_ver = ver;
+    return HMC_OK;
+  }
+
+  // dS_k/dphi at the current phi into `out` (level -1: all levels summed).
+  hmc_status level_grad(int k, double* out) {
+    HMC_TRY(tables());
+    ++nforce;
+    if (k == -1) {
+      HMC_TRY(gauss_grad(c, phi, 0, out));
+      for (int i = 0; i <= nmass; ++i) HMC_TRY(term_grad(c, nmass, masses, chi, i, o, out, &st));
+      return HMC_OK;
+    }
+    if (k == nmass) {
+      HMC_TRY(gauss_grad(c, phi, 0, out));
+    } else {
+      HMC_CUDA(c, cudaMemsetAsync(out, 0, N() * sizeof(double), c->stream));
+    }
+    return term_grad(c, nmass, masses, chi, k, o, out, &st);
+  }
+
+  void Q(double coef) {
+    if (err != HMC_OK) return;
+    err = axpy_real_launch(c, (int)N(), coef, pi, phi);
+    ++ver;
+  }
+
+  // The force of level k at the current field, computed unless cached.
+  double* ensure(int k) {
+    const int slot = k < 0 ? nmass + 1 : k;
+    double* f = cache + (size_t)slot * N();
+    if (cache_ver[slot] != ver) {
+      err = level_grad(k, f);
+      if (err != HMC_OK) return nullptr;
+      cache_ver[slot] = ver;
+    }
+    return f;
+  }
+
+  void P(int k, double coef) {
+    if (err != HMC_OK) return;
+    double* f = ensure(k);
+    if (f) err = axpy_real_launch(c, (int)N(), -coef, f, pi);
+  }
+};
+
+// Nested Omelyan (Section 5.2) over levels with steps[k] steps per trajectory.
+struct Nested {
+  MD& md;
+  std::vector<int> ratio;
+  int L;
+  double zeta;
+
+  void inner_first(int k, double h) {
+    if (k == L - 1) {
+      md.Q(0.5 * h);
+      return;
+    }
+    const int r = ratio[k + 1];
+    const double hh = h / r;
+    for (int i = 0; i < r / 2; ++i) step(k + 1, hh);
+    if (r % 2) half_first(k + 1, hh);
+  }
+  void inner_second(int k, double h) {
+    if (k == L - 1) {
+      md.Q(0.5 * h);
+      return;
+    }
+    const int r = ratio[k + 1];
+    const double hh = h / r;
+    if (r % 2) half_second(k + 1, hh);
+    for (int i = 0; i < r / 2; ++i) step(k + 1, hh);
+  }
+  void step(int k, double h) {
+    md.P(k, zeta * h);
+    inner_first(k, h);
+    md.P(k, (1.0 - 2.0 * zeta) * h);
+    inner_second(k, h);
+    md.P(k, zeta * h);
+  }
+  void half_first(int k, double h) {
+    md.P(k, zeta * h);
+    inner_first(k, h);
+    md.P(k, 0.5 * (1.0 - 2.0 * zeta) * h);
+  }
+  void half_second(int k, double h) {
+    md.P(k, 0.5 * (1.0 - 2.0 * zeta) * h);
+    inner_second(k, h);
+    md.P(k, zeta * h);
+  }
+};
+
+}  // namespace hmc
+
+using namespace hmc;
+
+extern "C" hmc_status hmc_md_trajectory(hmc_ctx* c, double* phi, double* pi, int nmass,
+                                        const double* masses, const void* const* rho,
+                                        const hmc_integrator* integ, const hmc_solver_opts* md_opts,
+                                        const hmc_solver_opts* action_opts, double* H0, double* H1,
+                                        hmc_solve_info* agg) {
+  if (!c) return HMC_ERR_INVALID;
+  if (!phi || !pi || !integ || !md_opts || !action_opts || !H0 || !H1 || !rho)
+    return fail(c, HMC_ERR_INVALID, "NULL argument");
+  if (((uintptr_t)phi) % 8 || ((uintptr_t)pi) % 8) return fail(c, HMC_ERR_INVALID, "phi/pi misaligned");
+  HMC_TRY(check_masses(c, nmass, masses));
+  for (int i = 0; i <= nmass; ++i)
+    if (!rho[i] || ((uintptr_t)rho[i]) % 16) return fail(c, HMC_ERR_INVALID, "rho entry NULL or misaligned");
+  if (integ->nmd < 1 || !(integ->tau > 0.0)) return fail(c, HMC_ERR_INVALID, "bad nmd or tau");
+  std::vector<int> steps;
+  if (integ->kind == HMC_INTEG_NESTED_OMELYAN) {
+    for (int k = 0; k < nmass; ++k) {
+      const int Nk = integ->N[k];
+      if (Nk < 1) return fail(c, HMC_ERR_INVALID, "time-scale ratio N_k must be >= 1");
+      if (k == 0 && integ->nmd % Nk) return fail(c, HMC_ERR_INVALID, "N_0 must divide N_MD");
+      if (k > 0 && integ->N[k - 1] % Nk) return fail(c, HMC_ERR_INVALID, "N_k must divide N_{k-1}");
+      steps.push_back(integ->nmd / Nk);
+    }
+    steps.push_back(integ->nmd);
+  } else if (integ->kind != HMC_INTEG_LEAPFROG && integ->kind != HMC_INTEG_FORCE_GRADIENT) {
+    return fail(c, HMC_ERR_INVALID, "unknown integrator");
+  }
+  const size_t N = (size_t)c->geo.N;
+  const size_t vb = sizeof(double2) * N;
+  double2* chibuf;
+  double* cache;
+  HMC_TRY(ws_get(c, WS_MD_CHI, vb * (nmass + 1), (void**)&chibuf));
+  HMC_TRY(ws_get(c, WS_MD_FORCE, sizeof(double) * N * (nmass + 2), (void**)&cache));
+  std::vector<double2*> chi(nmass + 1);
+  for (int i = 0; i <= nmass; ++i) chi[i] = chibuf + i * N;
+
+  MD md{c, phi, pi, nmass, masses, chi.data(), md_opts, cache};
+  md.cache_ver.assign(nmass + 2, -1);
+  if (agg) std::memset(agg, 0, sizeof(*agg));
+
+  // pseudofermions from rho at the starting field
+  HMC_TRY(md.tables());
+  SolveStats chist;
+  hmc_status s = make_chi(c, nmass, masses, (const double2* const*)rho, chi.data(), action_opts, &chist);
+  if (s != HMC_OK) return s;
+
+  // H0 = phi^2/(2 delta U) + sum rho^dagger rho + pi^2/2
+  const double inv_dU = 1.0 / (c->delta * c->lat.U);
+  HMC_TRY(half_sq_launch(c, (int)N, phi, inv_dU, pi, c->dscal + 54, c->tickets));
+  for (int i = 0; i <= nmass; ++i)
+    HMC_TRY(norm2_launch(c, (int)N, (const double2*)rho[i], c->dscal + 56 + i, c->tickets));
+  HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 54, c->dscal + 54, sizeof(double) * (2 + nmass + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+  HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+  double h0 = c->dscal_host[54] + c->dscal_host[55];
+  for (int i = 0; i <= nmass; ++i) h0 += c->dscal_host[56 + i];
+
+  // molecular dynamics
+  const double tau = integ->tau;
+  if (integ->kind == HMC_INTEG_NESTED_OMELYAN) {
+    Nested nest{md, {}, (int)steps.size(), integ->zeta};
+    nest.ratio.push_back(steps[0]);
+    for (size_t k = 1; k < steps.size(); ++k) nest.ratio.push_back(steps[k] / steps[k - 1]);
+    const double h0s = tau / steps[0];
+    for (int i = 0; i < steps[0] && md.err == HMC_OK; ++i) nest.step(0, h0s);
+  } else if (integ->kind == HMC_INTEG_LEAPFROG) {
+    const double h = tau / integ->nmd;
+    for (int i = 0; i < integ->nmd && md.err == HMC_OK; ++i) {
+      md.Q(0.5 * h);
+      md.P(-1, h);
+      md.Q(0.5 * h);
+    }
+  } else {
+    // force gradient, Eq. force_cal: the middle kick uses the force at
+    // phi_tilde = phi - (h^2/24) dS/dphi(phi)
+    const double h = tau / integ->nmd;
+    double* phit;
+    HMC_TRY(ws_get(c, WS_MD_PHI0, sizeof(double) * N, (void**)&phit));
+    for (int i = 0; i < integ->nmd && md.err == HMC_OK; ++i) {
+      md.P(-1, h / 6.0);
+      md.Q(0.5 * h);
+      const double* g1 = md.ensure(-1);
+      if (!g1) break;
+      HMC_CUDA(c, cudaMemcpyAsync(phit, phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+      HMC_TRY(axpy_real_launch(c, (int)N, -(h * h / 24.0), g1, phit));
+      // kick with the force at phi_tilde, then return to phi (new versions so
+      // that neither the tables nor the cache of one field serve the other)
+      md.phi = phit;
+      ++md.ver;
+      md.P(-1, (2.0 / 3.0) * h);
+      md.phi = phi;
+      ++md.ver;
+      md.Q(0.5 * h);
+      md.P(-1, h / 6.0);
+    }
+  }
+  if (md.err != HMC_OK) return md.err;
+
+  // H1 = S(phi') + pi'^2/2 with the action solves at action_opts' tolerance
+  HMC_TRY(md.tables());
+  SolveStats hst;
+  HMC_TRY(half_sq_launch(c, (int)N, phi, inv_dU, pi, c->dscal + 54, c->tickets));
+  for (int i = 0; i <= nmass; ++i) {
+    s = term_action(c, nmass, masses, chi.data(), i, action_opts, c->dscal + 56 + i, &hst);
+    if (s != HMC_OK) return s;
+  }
+  HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 54, c->dscal + 54, sizeof(double) * (2 + nmass + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+  HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+  double h1 = c->dscal_host[54] + c->dscal_host[55];
+  for (int i = 0; i <= nmass; ++i) h1 += c->dscal_host[56 + i];
+  *H0 = h0;
+  *H1 = h1;
+  if (agg) {
+    SolveStats all = md.st;
+    all.iters += chist.iters + hst.iters;
+    all.outer += chist.outer + hst.outer;
+    all.inner += chist.inner + hst.inner;
+    all.applies64 += chist.applies64 + hst.applies64;
+    all.applies32 += chist.applies32 + hst.applies32;
+    agg->iters = all.iters;
+    agg->iters_outer = all.outer;
+    agg->iters_inner = all.inner;
+    agg->applies64 = all.applies64;
+    agg->applies32 = all.applies32;
+    agg->status = HMC_OK;
+    agg->true_rel_res = hst.true_rel;
+    agg->bytes = (long long)((double)N * (192.0 * all.applies64 + 96.0 * all.applies32));
+  }
+  return HMC_OK;
+}

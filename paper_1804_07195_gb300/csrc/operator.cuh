@@ -1,0 +1,110 @@
+// The fermion operator M[phi; m_s] of Eq. ferm_op and its adjoint, as device
+// code. One thread handles one cell-time q: the A row q and the B row H + q.
+//
+//   (M u)_A(x,t)  = -u_A(x,t) + s (e^{+i phi_A(x,t)} - delta m_s) u_A(x,t-1)
+//                   - delta kappa [u_B(i,j) + u_B(i-1,j) + u_B(i,j-1)](t)
+//   (M u)_B(x,t)  = +u_B(x,t) - s (e^{-i phi_B(x,t)} - delta m_s) u_B(x,t+1)
+//                   - delta kappa [u_A(i,j) + u_A(i+1,j) + u_A(i,j+1)](t)
+//   (M^+ p)_A(x,t) = -p_A(x,t) + s (e^{-i phi_A(x,t+1)} - delta m_s) p_A(x,t+1) - delta kappa sum_B
+//   (M^+ p)_B(x,t) = +p_B(x,t) - s (e^{+i phi_B(x,t-1)} - delta m_s) p_B(x,t-1) - delta kappa sum_A
+// with s = -1 on the hop that wraps around the time circle (anti-periodic).
+#pragma once
+
+#include "common.cuh"
+
+namespace hmc {
+
+// e^{i phi_k}. FP64: read from a table built once per field. FP32: computed
+// from the field rounded to float, with the argument reduced to [-pi, pi] and
+// the hardware sine/cosine (absolute error about 4e-7 there), which is below
+// what the single-precision inner solver needs.
+template <typename R>
+struct Phase;
+
+template <>
+struct Phase<double> {
+  const double2* E;
+  __device__ __forceinline__ Cx<double> operator()(int k) const {
+    double2 e = E[k];
+    return Cx<double>{e.x, e.y};
+  }
+};
+
+template <>
+struct Phase<float> {
+  const float* phi;
+  __device__ __forceinline__ Cx<float> operator()(int k) const {
+    float x = phi[k];
+    x = fmaf(-6.28318530717958648f, rintf(x * 0.159154943091895336f), x);
+    float s, c;
+    __sincosf(x, &s, &c);
+    return Cx<float>{c, s};
+  }
+};
+
+// c + z v with fused multiply-adds.
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma(Cx<R> z, Cx<R> v, Cx<R> c) {
+  Cx<R> o;
+  o.re = fma(z.re, v.re, fma(-z.im, v.im, c.re));
+  o.im = fma(z.re, v.im, fma(z.im, v.re, c.im));
+  return o;
+}
+
+// t - dk (a + b + c)
+template <typename R>
+__device__ __forceinline__ Cx<R> hopsum(Cx<R> t, R dk, Cx<R> a, Cx<R> b, Cx<R> c) {
+  Cx<R> o;
+  o.re = fma(-dk, a.re + b.re + c.re, t.re);
+  o.im = fma(-dk, a.im + b.im + c.im, t.im);
+  return o;
+}
+
+template <typename R>
+struct PairOut {
+  Cx<R> a, b;
+};
+
+// M^dagger applied at the cell-time of nb, reading p (precision R).
+template <typename R>
+__device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const Phase<R>& ph, R dm,
+                                                const typename Vec2<R>::type* __restrict__ p,
+                                                const Nbr& nb) {
+  const int H = g.H;
+  const R dk = (R)g.dk;
+  Cx<R> pa = ld<R>(p, nb.q), pb = ld<R>(p, H + nb.q);
+  // A row: time partner (x, t+1), phase of A at t+1, conjugated
+  Cx<R> ea = ph(nb.tp);
+  Cx<R> za = cneg_if(Cx<R>{ea.re - dm, -ea.im}, nb.wrap_tp);
+  Cx<R> ta = cfma(za, ld<R>(p, nb.tp), Cx<R>{-pa.re, -pa.im});
+  Cx<R> oa = hopsum(ta, dk, pb, ld<R>(p, H + nb.im1), ld<R>(p, H + nb.jm1));
+  // B row: time partner (x, t-1), phase of B at t-1; the hop carries a minus sign
+  Cx<R> eb = ph(H + nb.tm);
+  Cx<R> zb = cneg_if(Cx<R>{dm - eb.re, -eb.im}, nb.wrap_tm);
+  Cx<R> tb = cfma(zb, ld<R>(p, H + nb.tm), pb);
+  Cx<R> ob = hopsum(tb, dk, pa, ld<R>(p, nb.ip1), ld<R>(p, nb.jp1));
+  return PairOut<R>{oa, ob};
+}
+
+// M applied at the cell-time of nb, reading u (precision R).
+template <typename R>
+__device__ __forceinline__ PairOut<R> m_pair(const Geo& g, const Phase<R>& ph, R dm,
+                                             const typename Vec2<R>::type* __restrict__ u,
+                                             const Nbr& nb) {
+  const int H = g.H;
+  const R dk = (R)g.dk;
+  Cx<R> ua = ld<R>(u, nb.q), ub = ld<R>(u, H + nb.q);
+  // A row: (e^{i phi_A(t)} - dm) u_A(t-1)
+  Cx<R> ea = ph(nb.q);
+  Cx<R> za = cneg_if(Cx<R>{ea.re - dm, ea.im}, nb.wrap_tm);
+  Cx<R> ta = cfma(za, ld<R>(u, nb.tm), Cx<R>{-ua.re, -ua.im});
+  Cx<R> oa = hopsum(ta, dk, ub, ld<R>(u, H + nb.im1), ld<R>(u, H + nb.jm1));
+  // B row: -(e^{-i phi_B(t)} - dm) u_B(t+1)
+  Cx<R> eb = ph(H + nb.q);
+  Cx<R> zb = cneg_if(Cx<R>{dm - eb.re, eb.im}, nb.wrap_tp);
+  Cx<R> tb = cfma(zb, ld<R>(u, H + nb.tp), ub);
+  Cx<R> ob = hopsum(tb, dk, ua, ld<R>(u, nb.ip1), ld<R>(u, nb.jp1));
+  return PairOut<R>{oa, ob};
+}
+
+}  // namespace hmc

@@ -1,0 +1,333 @@
+// Krylov solvers for A x = b, A = M_ms M_ms^dagger + sigma (Section 3 and
+// Algorithm A.1): CG in FP64 or FP32, and flexible GMRES with an FP32 CG
+// preconditioner. The iteration runs on the device; the host checks the
+// convergence flag every few iterations and only reads back small scalars.
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "solvers.h"
+
+namespace hmc {
+
+hmc_solver_opts default_opts() {
+  hmc_solver_opts o;
+  o.method = HMC_SOLVER_FGMRES_MIXED;
+  o.tol = 1e-10;
+  o.maxit = 100000;
+  o.restart = 10;
+  o.a = 5.0;
+  o.inner_floor = 1e-6;
+  o.inner_maxit = 2000;
+  return o;
+}
+
+void add_stats(hmc_solve_info* info, const SolveStats& s) {
+  if (!info) return;
+  info->iters += s.iters;
+  info->iters_outer += s.outer;
+  info->iters_inner += s.inner;
+  info->applies64 += s.applies64;
+  info->applies32 += s.applies32;
+  info->true_rel_res = s.true_rel;
+}
+
+template <typename R>
+static hmc_status vec_slots(hmc_ctx* c, V2<R>** r, V2<R>** p, V2<R>** u) {
+  const size_t bytes = sizeof(V2<R>) * (size_t)c->geo.N;
+  const bool d = sizeof(R) == 8;
+  HMC_TRY(ws_get(c, d ? WS_CG_R64 : WS_CG_R32, bytes, (void**)r));
+  HMC_TRY(ws_get(c, d ? WS_CG_P64 : WS_CG_P32, bytes, (void**)p));
+  HMC_TRY(ws_get(c, d ? WS_U64 : WS_U32, bytes, (void**)u));
+  return HMC_OK;
+}
+
+template <typename R>
+hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x, bool x_zero,
+                   double tol, int maxit, int sc_slot, bool want_true_res, SolveStats* st) {
+  const Geo& g = c->geo;
+  const R dm = (R)(c->delta * ms);
+  V2<R> *r, *p, *u;
+  HMC_TRY(vec_slots<R>(c, &r, &p, &u));
+  CGScal* sc = c->sc + sc_slot;
+  CGScal* sch = c->sc_host + sc_slot;
+  unsigned* tk = c->tickets;
+  const double tol2 = tol * tol;
+  if (x_zero) {
+    HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, tol2, maxit, sigma, tk));
+  } else {
+    HMC_TRY(mdag_launch<R>(c, g, dm, x, u));
+    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, p, sc, tol2, maxit, nullptr, tk));
+    if (sizeof(R) == 8) st->applies64++; else st->applies32++;
+  }
+  int chunk = 4;
+  int launched = 0;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      HMC_TRY(cg_mdag_launch<R>(c, g, dm, p, u, sc, tk));
+      HMC_TRY(cg_m_launch<R>(c, g, dm, u, p, x, r, sc, tk));
+      HMC_TRY(cg_p_launch<R>(c, g.N, r, p, sc));
+    }
+    launched += chunk;
+    HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
+    HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sch->done != CG_RUNNING) break;
+    if (launched > maxit + 64) break;  // cannot happen: the device stops at maxit
+    if (chunk < 32) chunk *= 2;
+  }
+  st->iters += sch->iter;
+  if (sizeof(R) == 8) st->applies64 += sch->iter; else st->applies32 += sch->iter;
+  st->cg_done = sch->done;
+  if (want_true_res) {
+    HMC_TRY(mdag_launch<R>(c, g, dm, x, u));
+    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, nullptr, nullptr, 0.0, 0, c->dscal, tk));
+    HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host, c->dscal, 2 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double rr = c->dscal_host[0], bb = c->dscal_host[1];
+    st->true_rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    if (sizeof(R) == 8) st->applies64++; else st->applies32++;
+  }
+  if (sch->done == CG_BREAKDOWN) return fail(c, HMC_ERR_NAN, "CG breakdown: non-positive or non-finite curvature/residual");
+  if (sch->done == CG_MAXIT) return fail(c, HMC_ERR_NOT_CONVERGED, "CG reached its iteration limit");
+  return HMC_OK;
+}
+
+template hmc_status cg_core<double>(hmc_ctx*, double, double, const double2*, double2*, bool, double,
+                                    int, int, bool, SolveStats*);
+template hmc_status cg_core<float>(hmc_ctx*, double, double, const float2*, float2*, bool, double,
+                                   int, int, bool, SolveStats*);
+
+hmc_status apply_A64(hmc_ctx* c, double ms, double sigma, const double2* in, double2* out) {
+  double2* u;
+  HMC_TRY(ws_get(c, WS_U64, sizeof(double2) * (size_t)c->geo.N, (void**)&u));
+  const double dm = c->delta * ms;
+  HMC_TRY(mdag_launch<double>(c, c->geo, dm, in, u));
+  return m_launch<double>(c, c->geo, dm, u, sigma != 0.0 ? in : nullptr, sigma, out);
+}
+
+// Solve the small least-squares problem of Algorithm A.1 through the normal
+// equations (h^H h) y = |r| h^H e1 with a Cholesky factorisation (Appendix A).
+// h is (k+1) x k, column-major in H[i + j*(ldh)].
+static bool normal_eq_cholesky(const std::vector<std::complex<double>>& H, int ldh, int k,
+                               double rnorm, std::vector<std::complex<double>>& y) {
+  using cd = std::complex<double>;
+  std::vector<cd> G((size_t)k * k), rhs(k);
+  for (int a = 0; a < k; ++a) {
+    for (int b = 0; b < k; ++b) {
+      cd s = 0;
+      for (int i = 0; i <= k; ++i) s += std::conj(H[i + a * ldh]) * H[i + b * ldh];
+      G[a + b * k] = s;
+    }
+    rhs[a] = rnorm * std::conj(H[0 + a * ldh]);
+  }
+  // G = L L^H
+  std::vector<cd> L((size_t)k * k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    double d = std::real(G[j + j * k]);
+    for (int p = 0; p < j; ++p) d -= std::norm(L[j + p * k]);
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[j + j * k] = ljj;
+    for (int i = j + 1; i < k; ++i) {
+      cd s = G[i + j * k];
+      for (int p = 0; p < j; ++p) s -= L[i + p * k] * std::conj(L[j + p * k]);
+      L[i + j * k] = s / ljj;
+    }
+  }
+  std::vector<cd> z(k);
+  for (int i = 0; i < k; ++i) {
+    cd s = rhs[i];
+    for (int p = 0; p < i; ++p) s -= L[i + p * k] * z[p];
+    z[i] = s / L[i + i * k];
+  }
+  y.assign(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    cd s = z[i];
+    for (int p = i + 1; p < k; ++p) s -= std::conj(L[p + i * k]) * y[p];
+    y[i] = s / std::real(L[i + i * k]);
+  }
+  return true;
+}
+
+// Preconditioner solve z = A^{-1} v to relative tolerance t in precision prec
+// (32: spCG through float copies; 64: FP64 CG). t >= 1 gives z = v.
+static hmc_status precondition(hmc_ctx* c, double ms, double sigma, const double2* v64,
+                               const float2* v32, double2* z, double t, int prec, int inner_maxit,
+                               SolveStats* st) {
+  const int N = c->geo.N;
+  if (t >= 1.0) {
+    HMC_CUDA(c, cudaMemcpyAsync(z, v64, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+    return HMC_OK;
+  }
+  SolveStats in;
+  hmc_status s;
+  if (prec == 32) {
+    float2 *b32, *x32;
+    HMC_TRY(ws_get(c, WS_CG_B32, sizeof(float2) * N, (void**)&b32));
+    HMC_TRY(ws_get(c, WS_CG_X32, sizeof(float2) * N, (void**)&x32));
+    if (v32 == nullptr) {
+      HMC_TRY(to32_launch(c, N, v64, b32));
+      v32 = b32;
+    }
+    s = cg_core<float>(c, ms, sigma, v32, x32, true, t, inner_maxit, 1, false, &in);
+    if (s != HMC_OK && s != HMC_ERR_NOT_CONVERGED) return s;
+    HMC_TRY(to64_launch(c, N, x32, z));
+  } else {
+    s = cg_core<double>(c, ms, sigma, v64, z, true, t, inner_maxit, 1, false, &in);
+    if (s != HMC_OK && s != HMC_ERR_NOT_CONVERGED) return s;
+  }
+  c->err.clear();
+  st->inner += in.iters;
+  st->applies32 += in.applies32;
+  st->applies64 += in.applies64;
+  return HMC_OK;
+}
+
+hmc_status fgmres_core(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x, double tol,
+                       int restart, double a, int inner_prec, int maxit, double inner_floor,
+                       int inner_maxit, SolveStats* st) {
+  using cd = std::complex<double>;
+  const Geo& g = c->geo;
+  const int N = g.N;
+  const double dm = c->delta * ms;
+  const size_t vb = sizeof(double2) * (size_t)N;
+  double2 *r, *w, *u, *Vb, *Zb;
+  float2* v32 = nullptr;
+  HMC_TRY(ws_get(c, WS_FG_R, vb, (void**)&r));
+  HMC_TRY(ws_get(c, WS_FG_W, vb, (void**)&w));
+  HMC_TRY(ws_get(c, WS_U64, vb, (void**)&u));
+  HMC_TRY(ws_get(c, WS_FG_V, vb * restart, (void**)&Vb));
+  HMC_TRY(ws_get(c, WS_FG_Z, vb * restart, (void**)&Zb));
+  if (inner_prec == 32) HMC_TRY(ws_get(c, WS_CG_B32, sizeof(float2) * N, (void**)&v32));
+  unsigned* tk = c->tickets;
+  double* hdev = c->dscal;            // 2*restart doubles: h column; then |w|^2 at [40]
+  double* hhost = c->dscal_host;
+
+  // |b|
+  HMC_TRY(norm2_launch(c, N, b, hdev + 40, tk));
+  HMC_CUDA(c, cudaMemcpyAsync(hhost + 40, hdev + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double bnorm = std::sqrt(hhost[40]);
+  if (!std::isfinite(bnorm)) return fail(c, HMC_ERR_NAN, "FGMRES: right-hand side is not finite");
+  if (bnorm == 0.0) {
+    HMC_CUDA(c, cudaMemsetAsync(x, 0, vb, c->stream));
+    st->true_rel = 0.0;
+    return HMC_OK;
+  }
+  // first line of Algorithm A.1: spCG solve of A x = b (tolerance tol*a, floored)
+  HMC_TRY(precondition(c, ms, sigma, b, nullptr, x, std::max(tol * a, inner_floor), inner_prec,
+                       inner_maxit, st));
+  if (tol * a >= 1.0) HMC_CUDA(c, cudaMemsetAsync(x, 0, vb, c->stream));
+  // r = b - A x, ERR = |r|
+  auto true_residual = [&](double* err) -> hmc_status {
+    HMC_TRY(mdag_launch<double>(c, g, dm, x, u));
+    HMC_TRY(resid_launch<double>(c, g, dm, u, x, b, sigma, r, nullptr, nullptr, 0.0, 0, hdev + 40, tk));
+    HMC_CUDA(c, cudaMemcpyAsync(hhost + 40, hdev + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    st->applies64++;
+    *err = std::sqrt(hhost[40]);
+    return HMC_OK;
+  };
+  double err;
+  HMC_TRY(true_residual(&err));
+  if (!std::isfinite(err)) return fail(c, HMC_ERR_NAN, "FGMRES: residual is not finite");
+  int arnoldi = 0;
+  const int ldh = restart + 1;
+  std::vector<cd> H((size_t)ldh * restart), gvec(restart + 1), rs(restart);
+  std::vector<double> rc(restart);
+  while (err > tol * bnorm && arnoldi < maxit) {
+    const double rnorm = err;
+    std::fill(H.begin(), H.end(), cd(0));
+    std::fill(gvec.begin(), gvec.end(), cd(0));
+    gvec[0] = rnorm;
+    int k = 0;
+    double wnorm = rnorm;
+    const double2* wsrc = r;
+    for (int j = 0; j < restart; ++j) {
+      if (err < tol * bnorm) break;
+      double2* Vj = Vb + (size_t)j * N;
+      double2* Zj = Zb + (size_t)j * N;
+      // v_j = w / |w|
+      HMC_TRY(scale_launch(c, N, 1.0 / wnorm, wsrc, Vj, v32));
+      // z_j: spCG with tolerance TOL a |b| / ERR, or z_j = v_j
+      const double t = tol * a * bnorm / err;
+      HMC_TRY(precondition(c, ms, sigma, Vj, v32, Zj, t < 1.0 ? std::max(t, inner_floor) : 1.0,
+                           inner_prec, inner_maxit, st));
+      // w = A z_j, h_ij = v_i^H w (i <= j), w -= sum h_ij v_i, h_{j+1,j} = |w|
+      HMC_TRY(apply_A64(c, ms, sigma, Zj, w));
+      st->applies64++;
+      VecList V;
+      for (int i = 0; i <= j; ++i) V.v[i] = Vb + (size_t)i * N;
+      HMC_TRY(mdot_launch(c, N, V, j + 1, w, hdev, tk));
+      HMC_TRY(gsupd_launch(c, N, V, j + 1, hdev, w, hdev + 40, tk));
+      HMC_CUDA(c, cudaMemcpyAsync(hhost, hdev, 41 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+      for (int i = 0; i <= j; ++i) H[i + j * ldh] = cd(hhost[2 * i], hhost[2 * i + 1]);
+      wnorm = std::sqrt(hhost[40]);
+      H[j + 1 + j * ldh] = wnorm;
+      if (!std::isfinite(wnorm)) return fail(c, HMC_ERR_NAN, "FGMRES: Arnoldi vector is not finite");
+      // running residual estimate by Givens rotations
+      std::vector<cd> col(j + 2);
+      for (int i = 0; i <= j + 1; ++i) col[i] = H[i + j * ldh];
+      for (int i = 0; i < j; ++i) {
+        cd t0 = rc[i] * col[i] + rs[i] * col[i + 1];
+        col[i + 1] = -std::conj(rs[i]) * col[i] + rc[i] * col[i + 1];
+        col[i] = t0;
+      }
+      double cr;
+      cd sr;
+      if (std::abs(col[j + 1]) == 0.0) {
+        cr = 1.0;
+        sr = 0.0;
+      } else if (std::abs(col[j]) == 0.0) {
+        cr = 0.0;
+        sr = std::conj(col[j + 1]) / std::abs(col[j + 1]);
+      } else {
+        const double na = std::abs(col[j]);
+        const double nrm = std::hypot(na, std::abs(col[j + 1]));
+        cr = na / nrm;
+        sr = (col[j] / na) * std::conj(col[j + 1]) / nrm;
+      }
+      rc[j] = cr;
+      rs[j] = sr;
+      gvec[j + 1] = -std::conj(sr) * gvec[j];
+      gvec[j] = cr * gvec[j];
+      err = std::abs(gvec[j + 1]);
+      k = j + 1;
+      wsrc = w;
+      ++arnoldi;
+      if (arnoldi >= maxit) break;
+    }
+    if (k == 0) break;
+    std::vector<cd> y;
+    if (!normal_eq_cholesky(H, ldh, k, rnorm, y))
+      return fail(c, HMC_ERR_NAN, "FGMRES: normal equations not positive definite");
+    VecList Z;
+    CoefList coef;
+    for (int i = 0; i < k; ++i) {
+      Z.v[i] = Zb + (size_t)i * N;
+      coef.re[i] = y[i].real();
+      coef.im[i] = y[i].imag();
+    }
+    HMC_TRY(xupd_launch(c, N, Z, coef, k, x));
+    HMC_TRY(true_residual(&err));
+    st->outer++;
+  }
+  st->iters += arnoldi;
+  st->true_rel = err / bnorm;
+  if (!(err <= tol * bnorm)) return fail(c, HMC_ERR_NOT_CONVERGED, "FGMRES reached its step limit");
+  return HMC_OK;
+}
+
+hmc_status solve_opts(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x,
+                      const hmc_solver_opts* o, SolveStats* st) {
+  if (o->method == HMC_SOLVER_CG64)
+    return cg_core<double>(c, ms, sigma, b, x, true, o->tol, o->maxit, 0, true, st);
+  if (o->method == HMC_SOLVER_FGMRES_MIXED)
+    return fgmres_core(c, ms, sigma, b, x, o->tol, o->restart, o->a, 32, o->maxit, o->inner_floor,
+                       o->inner_maxit, st);
+  return fail(c, HMC_ERR_INVALID, "unknown solver method");
+}
+
+}  // namespace hmc

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/hmc.h declares; the Python binding declares the same set."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "hmc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hmc_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_07195_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_north_star_calls():
+    names = header_functions()
+    for f in ("hmc_apply_M", "hmc_apply_Mdag", "hmc_solve_cg", "hmc_solve_fgmres", "hmc_force",
+              "hmc_md_trajectory"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [f for f in header_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1804_07195_gb300 import _abi
+    assert sorted(_abi.PROTOTYPES) == header_functions()
+
+
+def test_host_only_calls(lib):
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    assert L.hmc_abi_version() == 1
+    assert L.hmc_status_string(0) == b"ok"
+    assert L.hmc_status_string(-3) == b"solver did not converge"
+    # invalid lattices are rejected before any CUDA call
+    h = ctypes.c_void_p()
+    bad = _abi.hmc_lattice(0, 3, 8, 1.0, 2.0, 4.0)
+    assert L.hmc_create(ctypes.byref(h), ctypes.byref(bad), None) == _abi.HMC_ERR_INVALID
+    bad = _abi.hmc_lattice(3, 3, 1, 1.0, 2.0, 4.0)
+    assert L.hmc_create(ctypes.byref(h), ctypes.byref(bad), None) == _abi.HMC_ERR_INVALID
+    assert L.hmc_destroy(None) == _abi.HMC_ERR_INVALID
+    assert L.hmc_apply_M(None, None, 0.0, None, None, 64) == _abi.HMC_ERR_INVALID
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1804_07195_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", src), f

@@ -1,0 +1,115 @@
+"""Parity of the CUDA solvers (Section 3, Algorithm A.1): the true residual
+|b - A x| / |b| evaluated by the oracle's operator is within the requested 1e-10,
+and the solution agrees with the oracle's LU solve on small lattices."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fermion as of
+from oracle import solvers as osv
+from oracle.lattice import Lattice as OLat
+
+from gpu_util import ctx_for, dev, host, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def true_rel(ol, phi, ms, sigma, x, b):
+    return osv.true_rel_residual(lambda v: of.apply_MMdag(ol, phi, ms, v, sigma), x, b)
+
+
+@pytest.mark.parametrize("name,ms,sigma", [("C1", 0.0, 0.0), ("C1", 0.3, 0.0), ("C1", 0.0, 0.09)])
+def test_cg_fp64_matches_lu(name, ms, sigma):
+    need_gpu()
+    w = W.workload(name)
+    ol = OLat.from_params(w.lat)
+    D = of.dense_M(ol, w.phi, ms)
+    x_ref = osv.dense_solve(D @ D.conj().T + sigma * np.eye(ol.N), w.b)
+    with ctx_for(w.lat) as ctx:
+        x, info = ctx.solve_cg(dev(w.phi), ms, dev(w.b), sigma=sigma, tol=1e-10)
+    x = host(x)
+    assert true_rel(ol, w.phi, ms, sigma, x, w.b) <= 1e-10
+    assert abs(info["true_rel_res"] - true_rel(ol, w.phi, ms, sigma, x, w.b)) < 1e-12
+    assert np.linalg.norm(x - x_ref) <= 1e-7 * np.linalg.norm(x_ref)
+    # the oracle's CG takes the same path: iteration counts agree closely
+    ref = osv.cg(lambda v: of.apply_MMdag(ol, w.phi, ms, v, sigma), w.b, tol=1e-10)
+    assert abs(info["iters"] - ref.iters) <= 2
+
+
+def test_cg_initial_guess_and_zero_rhs():
+    need_gpu()
+    w = W.workload("C1")
+    ol = OLat.from_params(w.lat)
+    with ctx_for(w.lat) as ctx:
+        phi, b = dev(w.phi), dev(w.b)
+        x, _ = ctx.solve_cg(phi, 0.0, b, tol=1e-10)
+        x2, info = ctx.solve_cg(phi, 0.0, b, x=x.clone(), tol=1e-10)
+        assert info["iters"] <= 1
+        z, info = ctx.solve_cg(phi, 0.0, torch.zeros_like(b), tol=1e-10)
+        assert info["iters"] == 0 and torch.count_nonzero(z) == 0
+
+
+def test_spcg_fp32():
+    need_gpu()
+    w = W.workload("C1")
+    ol = OLat.from_params(w.lat)
+    with ctx_for(w.lat) as ctx:
+        x, info = ctx.solve_spcg(dev(w.phi), 0.2, dev(w.b.astype(np.complex64)), tol=1e-5)
+    assert true_rel(ol, w.phi, 0.2, 0.0, host(x).astype(np.complex128), w.b.astype(np.complex64)) < 2e-5
+
+
+@pytest.mark.parametrize("name,ms", [("C1", 0.0), ("C3", 0.0), ("C3", 0.5)])
+def test_fgmres_mixed_true_residual(name, ms):
+    need_gpu()
+    w = W.workload(name)
+    ol = OLat.from_params(w.lat)
+    with ctx_for(w.lat) as ctx:
+        x, info = ctx.solve_fgmres(dev(w.phi), ms, dev(w.b), tol=1e-10)
+        xc, infoc = ctx.solve_cg(dev(w.phi), ms, dev(w.b), tol=1e-10)
+    x = host(x)
+    assert true_rel(ol, w.phi, ms, 0.0, x, w.b) <= 1e-10
+    assert info["iters_inner"] > 0 and info["applies32"] > info["applies64"]
+    # both solutions agree within what the residual bound allows
+    assert np.linalg.norm(x - host(xc)) <= 1e-6 * np.linalg.norm(x)
+
+
+def test_fgmres_iteration_structure_matches_oracle():
+    """Same Algorithm A.1 on both sides. FP32 rounding inside the inner solves
+    differs, so a restart that ends just above or just below TOL |b| on one side
+    may be repeated on the other: restarts agree within one, Arnoldi steps and
+    inner iterations closely."""
+    need_gpu()
+    w = W.workload("C1")
+    ol = OLat.from_params(w.lat)
+    A64 = lambda v: of.apply_MMdag(ol, w.phi, 0.0, v)
+    A32 = lambda v: of.apply_MMdag(ol, w.phi, 0.0, v.astype(np.complex64)).astype(np.complex64)
+    ref = osv.fgmres(A64, A32, w.b, tol=1e-10)
+    with ctx_for(w.lat) as ctx:
+        _, info = ctx.solve_fgmres(dev(w.phi), 0.0, dev(w.b), tol=1e-10)
+    assert abs(info["iters_outer"] - ref.outer_iters) <= 1, (info, ref.outer_iters)
+    assert abs(info["iters"] - ref.iters) <= 3 + 2 * abs(info["iters_outer"] - ref.outer_iters), (info, ref.iters)
+    assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters, (info, ref.inner_iters)
+
+
+def test_fgmres_fp64_inner_and_no_preconditioning():
+    need_gpu()
+    w = W.small(3, 3, 8, seed=3)
+    ol = OLat.from_params(w.lat)
+    with ctx_for(w.lat) as ctx:
+        x, info = ctx.solve_fgmres(dev(w.phi), 0.0, dev(w.b), tol=1e-11, inner_prec=64)
+        assert true_rel(ol, w.phi, 0.0, 0.0, host(x), w.b) <= 1e-11
+        x, info = ctx.solve_fgmres(dev(w.phi), 0.0, dev(w.b), tol=0.25)
+        assert info["iters_inner"] == 0
+        assert true_rel(ol, w.phi, 0.0, 0.0, host(x), w.b) <= 0.25
+
+
+def test_not_converged_is_reported():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C1")
+    with ctx_for(w.lat) as ctx:
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_cg(dev(w.phi), 0.0, dev(w.b), tol=1e-10, maxit=5)
+        assert e.value.status == -3
+        x, info = ctx.solve_cg(dev(w.phi), 0.0, dev(w.b), tol=1e-10, maxit=5, allow_fail=True)
+        assert info["iters"] == 5 and info["true_rel_res"] > 1e-10

@@ -29,6 +29,22 @@ def test_stencil_equals_dense_matrix(shape, ms):
     assert np.abs(AA @ x - fermion.apply_MMdag(lat, w.phi, ms, x, 0.25)).max() <= 1e-13 * ref
 
 
+@pytest.mark.parametrize("shape", SHAPES)
+def test_sparse_matrix_equals_dense_matrix(shape):
+    w = W.small(*shape, seed=12)
+    lat = Lattice.from_params(w.lat)
+    for ms in (0.0, 0.6):
+        assert np.abs(fermion.sparse_M(lat, w.phi, ms).toarray() - fermion.dense_M(lat, w.phi, ms)).max() < 1e-15
+
+
+def test_sparse_lu_solve_matches_dense_lu():
+    w = W.small(4, 5, 6, seed=13)
+    lat = Lattice.from_params(w.lat)
+    x1 = action.SolveA(lat, "splu")(w.phi, 0.3, w.b)
+    x2 = action.SolveA(lat, "dense")(w.phi, 0.3, w.b)
+    assert np.linalg.norm(x1 - x2) < 1e-11 * np.linalg.norm(x2)
+
+
 @pytest.mark.parametrize("shape", SHAPES[:4])
 def test_every_site_has_three_bonds(shape):
     lat = lat_of(*shape)

@@ -1,11 +1,740 @@
-// Batched solves of many independent systems (placeholder until the batched
-// kernels land).
+// Batched solves of many independent systems (M_s M_s^dagger + sigma_s) x_s = b_s,
+// lattices of uneven sizes, in one launch per kernel.
+//
+// Layout: the systems' vectors are concatenated; system s occupies sites
+// [off_s, off_s + N_s) in its own canonical order. Every block belongs to one
+// system (a block table maps block -> system), so a block's reduction partial
+// is per system and the last block of a system (per-system ticket) finishes
+// that system's scalars. A system that has converged is masked: its blocks
+// return at once. Chunks of CG iterations are captured into a CUDA graph and
+// replayed until every system is done.
+//
+// mixed = 0: CG in FP64 to |r| <= tol |b|.
+// mixed = 1: FP64 defect correction: r = b - A x in FP64, an FP32 CG solve of
+//            A e = r, x += e, repeated until the FP64 true residual meets tol.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "operator.cuh"
 #include "solvers.h"
+
+namespace hmc {
+
+struct BSys {
+  Geo g;
+  long long off;     // first site of the system in the concatenated vectors
+  int block0, nblocks;
+  double dm, sigma;
+  const double* phi; // the caller's field (phase kernel only)
+  int maxit;         // iteration limit of this system's CG
+  int pad;
+};
+
+struct BState {
+  CGScal cg;
+  int active;  // 1 while the system takes part in the current inner solve
+  int pad;
+};
+
+// Sum K values over the blocks [base, base + count) of one system, in a fixed
+// order; true in the last block of the group (totals in thread 0).
+template <int K>
+__device__ __forceinline__ bool group_sum(double (&v)[K], double* partials, int base, int count,
+                                          unsigned* ticket, double (&tot)[K]) {
+  __shared__ double smem[K * 32];
+  __shared__ bool am_last;
+  block_sum<K>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)k * gridDim.x + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == (unsigned)count - 1u);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < count; b += blockDim.x) acc += __ldcg(&partials[(size_t)k * gridDim.x + base + b]);
+    w[k] = acc;
+  }
+  block_sum<K>(w, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = w[k];
+    *ticket = 0u;
+  }
+  return true;
+}
+
+#define BLOCK_SYS()                                  \
+  __shared__ BSys S_;                                \
+  const int s_ = bsys[blockIdx.x];                   \
+  if (threadIdx.x == 0) S_ = sys[s_];                \
+  __syncthreads();                                   \
+  const Geo& g = S_.g;                               \
+  const int lb = blockIdx.x - S_.block0;             \
+  const int stride = S_.nblocks * blockDim.x
+
+__global__ void kb_phase(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                         double2* __restrict__ E, float* __restrict__ phi32) {
+  BLOCK_SYS();
+  for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
+    double x = S_.phi[k], s, c;
+    sincos(x, &s, &c);
+    E[S_.off + k] = make_double2(c, s);
+    phi32[S_.off + k] = (float)x;
+  }
+}
+
+template <typename R>
+struct BPhase;
+template <>
+struct BPhase<double> {
+  static __device__ __forceinline__ Phase<double> at(const double2* E, const float*, long long off) {
+    return Phase<double>{E + off};
+  }
+};
+template <>
+struct BPhase<float> {
+  static __device__ __forceinline__ Phase<float> at(const double2*, const float* p32, long long off) {
+    return Phase<float>{p32 + off};
+  }
+};
+
+// x = 0, r = p = b; |b|^2; state init with thresh = tol2[s] |b|^2 (inactive
+// systems are marked done).
+template <typename R>
+__global__ void kb_init(const BSys* __restrict__ sys, const int* __restrict__ bsys, BState* bst,
+                        const double* __restrict__ tol2, const V2<R>* __restrict__ b, V2<R>* __restrict__ x,
+                        V2<R>* __restrict__ r, V2<R>* __restrict__ p, int maxit, double* partials,
+                        unsigned* tickets) {
+  BLOCK_SYS();
+  double acc[1] = {0.0};
+  for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
+    const long long i = S_.off + k;
+    Cx<R> bk = ld<R>(b, i);
+    st(x, i, Cx<R>{(R)0, (R)0});
+    st(r, i, bk);
+    st(p, i, bk);
+    acc[0] += (double)norm2(bk);
+  }
+  double tot[1];
+  if (group_sum<1>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+    CGScal& c = bst[s_].cg;
+    c.rr = c.bb = tot[0];
+    c.thresh = tol2[s_] * tot[0];
+    c.sigma = S_.sigma;
+    c.iter = 0;
+    c.maxit = min(maxit, S_.maxit);
+    c.alpha = c.beta = c.pAp = 0.0;
+    c.done = (!bst[s_].active || tot[0] <= c.thresh) ? CG_CONVERGED : CG_RUNNING;
+    if (!isfinite(tot[0])) c.done = CG_BREAKDOWN;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) kb_cg_mdag(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                  BState* bst, const double2* __restrict__ E,
+                                                  const float* __restrict__ p32, const V2<R>* __restrict__ p,
+                                                  V2<R>* __restrict__ u, double* partials, unsigned* tickets,
+                                                  unsigned* ndone) {
+  BLOCK_SYS();
+  if (bst[s_].cg.done) return;
+  const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
+  const R dm = (R)S_.dm, sigma = (R)S_.sigma;
+  const V2<R>* ps = p + S_.off;
+  V2<R>* us = u + S_.off;
+  double acc[1] = {0.0};
+  for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = mdag_pair<R>(g, ph, dm, ps, nb);
+    st(us, q, o.a);
+    st(us, g.H + q, o.b);
+    R loc = norm2(o.a) + norm2(o.b);
+    if (sigma != (R)0) loc += sigma * (norm2(ld<R>(ps, q)) + norm2(ld<R>(ps, g.H + q)));
+    acc[0] += (double)loc;
+  }
+  double tot[1];
+  if (group_sum<1>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+    CGScal& c = bst[s_].cg;
+    c.pAp = tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      c.alpha = 0.0;
+      c.done = CG_BREAKDOWN;
+      atomicAdd(ndone, 1u);
+    } else {
+      c.alpha = c.rr / tot[0];
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                               BState* bst, const double2* __restrict__ E,
+                                               const float* __restrict__ p32, const V2<R>* __restrict__ u,
+                                               const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
+                                               V2<R>* __restrict__ r, double* partials, unsigned* tickets,
+                                               unsigned* ndone) {
+  BLOCK_SYS();
+  if (bst[s_].cg.done) return;
+  const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
+  const R dm = (R)S_.dm, sigma = (R)S_.sigma, alpha = (R)bst[s_].cg.alpha;
+  const V2<R>* us = u + S_.off;
+  double acc[1] = {0.0};
+  for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
+    Nbr nb = neighbours(g, q);
+    PairOut<R> o = m_pair<R>(g, ph, dm, us, nb);
+    R loc = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long k = S_.off + (h ? g.H + q : q);
+      Cx<R> Ap = h ? o.b : o.a;
+      Cx<R> pk = ld<R>(p, k), xk = ld<R>(x, k), rk = ld<R>(r, k);
+      Ap.re = fma(sigma, pk.re, Ap.re);
+      Ap.im = fma(sigma, pk.im, Ap.im);
+      xk.re = fma(alpha, pk.re, xk.re);
+      xk.im = fma(alpha, pk.im, xk.im);
+      rk.re = fma(-alpha, Ap.re, rk.re);
+      rk.im = fma(-alpha, Ap.im, rk.im);
+      st(x, k, xk);
+      st(r, k, rk);
+      loc += norm2(rk);
+    }
+    acc[0] += (double)loc;
+  }
+  double tot[1];
+  if (group_sum<1>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+    CGScal& c = bst[s_].cg;
+    const double rr = tot[0];
+    c.beta = rr / c.rr;
+    c.rr = rr;
+    c.iter += 1;
+    if (!isfinite(rr))
+      c.done = CG_BREAKDOWN;
+    else if (rr <= c.thresh)
+      c.done = CG_CONVERGED;
+    else if (c.iter >= c.maxit)
+      c.done = CG_MAXIT;
+    if (c.done) atomicAdd(ndone, 1u);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) kb_cg_p(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                               const BState* bst, const V2<R>* __restrict__ r,
+                                               V2<R>* __restrict__ p) {
+  BLOCK_SYS();
+  if (bst[s_].cg.done) return;
+  const R beta = (R)bst[s_].cg.beta;
+  for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
+    const long long i = S_.off + k;
+    Cx<R> rk = ld<R>(r, i), pk = ld<R>(p, i);
+    pk.re = fma(beta, pk.re, rk.re);
+    pk.im = fma(beta, pk.im, rk.im);
+    st(p, i, pk);
+  }
+}
+
+// FP64 u = M^dagger x for every system (plain)
+__global__ void __launch_bounds__(512) kb_mdag64(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                 const double2* __restrict__ E, const double2* __restrict__ x,
+                                                 double2* __restrict__ u) {
+  BLOCK_SYS();
+  const Phase<double> ph{E + S_.off};
+  for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
+    Nbr nb = neighbours(g, q);
+    PairOut<double> o = mdag_pair<double>(g, ph, S_.dm, x + S_.off, nb);
+    st(u + S_.off, q, o.a);
+    st(u + S_.off, g.H + q, o.b);
+  }
+}
+
+// FP64 r = b - (M u + sigma x), per-system |r|^2, |b|^2 into rrbb[2 s]; the
+// FP32 copy r32 = r (the right-hand side of the next inner solve).
+__global__ void __launch_bounds__(512) kb_resid64(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                  const double2* __restrict__ E, const double2* __restrict__ u,
+                                                  const double2* __restrict__ x, const double2* __restrict__ b,
+                                                  double2* __restrict__ r, float2* __restrict__ r32,
+                                                  double* rrbb, double* partials, unsigned* tickets) {
+  BLOCK_SYS();
+  const Phase<double> ph{E + S_.off};
+  double acc[2] = {0.0, 0.0};
+  for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
+    Nbr nb = neighbours(g, q);
+    PairOut<double> o = m_pair<double>(g, ph, S_.dm, u + S_.off, nb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long k = S_.off + (h ? g.H + q : q);
+      Cx<double> Ax = h ? o.b : o.a;
+      double2 xk = x[k], bk = b[k];
+      double2 rk = make_double2(bk.x - fma(S_.sigma, xk.x, Ax.re), bk.y - fma(S_.sigma, xk.y, Ax.im));
+      r[k] = rk;
+      if (r32) r32[k] = make_float2((float)rk.x, (float)rk.y);
+      acc[0] = fma(rk.x, rk.x, fma(rk.y, rk.y, acc[0]));
+      acc[1] = fma(bk.x, bk.x, fma(bk.y, bk.y, acc[1]));
+    }
+  }
+  double tot[2];
+  if (group_sum<2>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+    rrbb[2 * s_] = tot[0];
+    rrbb[2 * s_ + 1] = tot[1];
+  }
+}
+
+// x += (double) e for active systems
+__global__ void __launch_bounds__(512) kb_xadd(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                               const BState* bst, const float2* __restrict__ e,
+                                               double2* __restrict__ x) {
+  BLOCK_SYS();
+  if (!bst[s_].active) return;
+  for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
+    const long long i = S_.off + k;
+    float2 ev = e[i];
+    double2 xv = x[i];
+    x[i] = make_double2(xv.x + (double)ev.x, xv.y + (double)ev.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+struct BatchWs {
+  long long Ntot = 0;
+  int nsys = 0;
+  int blocks = 0;
+  int threads = 256;
+  std::vector<BSys> hsys;
+  std::vector<int> hbsys;
+  BSys* sys = nullptr;
+  int* bsys = nullptr;
+  BState* st = nullptr;
+  BState* st_host = nullptr;
+  double* tol2 = nullptr;
+  double* rrbb = nullptr;
+  double* rrbb_host = nullptr;
+  unsigned* tickets = nullptr;
+  unsigned* ndone = nullptr;
+  unsigned* ndone_host = nullptr;
+  double* partials = nullptr;
+  double2 *E = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *u = nullptr;
+  float *phi32 = nullptr;
+  float2 *r32 = nullptr, *e32 = nullptr, *p32v = nullptr, *u32 = nullptr, *rr32 = nullptr;
+  std::vector<void*> allocs;
+};
+
+static hmc_status bmalloc(hmc_ctx* c, BatchWs& w, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HMC_ERR_NOMEM, "batched workspace allocation failed");
+  }
+  w.allocs.push_back(*p);
+  return HMC_OK;
+}
+
+static void bfree(BatchWs& w) {
+  for (void* p : w.allocs) cudaFree(p);
+  w.allocs.clear();
+  if (w.st_host) cudaFreeHost(w.st_host);
+  if (w.rrbb_host) cudaFreeHost(w.rrbb_host);
+  if (w.ndone_host) cudaFreeHost(w.ndone_host);
+  w.st_host = nullptr;
+  w.rrbb_host = nullptr;
+  w.ndone_host = nullptr;
+}
+
+// Build the block table for `threads` threads per block and `ipt` cell-times
+// per thread; returns the total block count.
+static int plan_blocks(BatchWs& w, int threads, int ipt) {
+  int b = 0;
+  w.hbsys.clear();
+  for (int s = 0; s < w.nsys; ++s) {
+    BSys& S = w.hsys[s];
+    const long long work = std::max(S.g.H, 1);
+    int nb = (int)((work + (long long)threads * ipt - 1) / ((long long)threads * ipt));
+    nb = std::max(nb, 1);
+    S.block0 = b;
+    S.nblocks = nb;
+    for (int i = 0; i < nb; ++i) w.hbsys.push_back(s);
+    b += nb;
+  }
+  w.blocks = b;
+  w.threads = threads;
+  return b;
+}
+
+// Kernel sequence of one CG iteration for all systems, in precision R.
+template <typename R>
+static void cg_iteration(const BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p, V2<R>* u) {
+  const dim3 G(w.blocks), T(w.threads);
+  kb_cg_mdag<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, p, u, w.partials, w.tickets, w.ndone);
+  kb_cg_m<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, u, p, x, r, w.partials, w.tickets, w.ndone);
+  kb_cg_p<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, r, p);
+}
+
+// Tuned (threads, cell-times per thread) per precision and size bucket.
+struct TuneKey {
+  int prec, bucket;
+  bool operator<(const TuneKey& o) const { return prec != o.prec ? prec < o.prec : bucket < o.bucket; }
+};
+static std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+template <typename R>
+static hmc_status upload_plan(hmc_ctx* c, BatchWs& w, cudaStream_t s) {
+  HMC_CUDA(c, cudaMemcpyAsync(w.sys, w.hsys.data(), sizeof(BSys) * w.nsys, cudaMemcpyHostToDevice, s));
+  HMC_CUDA(c, cudaMemcpyAsync(w.bsys, w.hbsys.data(), sizeof(int) * w.blocks, cudaMemcpyHostToDevice, s));
+  return HMC_OK;
+}
+
+// Time a few CG iterations of each candidate block shape on this batch and
+// keep the fastest for the (precision, size) bucket.
+template <typename R>
+static hmc_status autotune(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p,
+                           V2<R>* u, const V2<R>* b, int* threads, int* ipt) {
+  const int bucket = (int)std::log2((double)std::max<long long>(w.Ntot, 2));
+  TuneKey key{(int)sizeof(R), bucket};
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    *threads = it->second.first;
+    *ipt = it->second.second;
+    return HMC_OK;
+  }
+  const int cand[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+  cudaEvent_t e0, e1;
+  HMC_CUDA(c, cudaEventCreate(&e0));
+  HMC_CUDA(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = 256, bi = 2;
+  for (auto& cd : cand) {
+    plan_blocks(w, cd[0], cd[1]);
+    HMC_TRY(upload_plan<R>(c, w, s));
+    HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * w.nsys, s));
+    kb_init<R><<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.st, w.tol2, b, x, r, p, 1 << 30,
+                                               w.partials, w.tickets);
+    cg_iteration<R>(w, s, x, r, p, u);
+    HMC_CUDA(c, cudaEventRecord(e0, s));
+    for (int i = 0; i < 3; ++i) cg_iteration<R>(w, s, x, r, p, u);
+    HMC_CUDA(c, cudaEventRecord(e1, s));
+    HMC_CUDA(c, cudaEventSynchronize(e1));
+    HMC_CUDA(c, cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bt = cd[0];
+      bi = cd[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tuned[key] = {bt, bi};
+  *threads = bt;
+  *ipt = bi;
+  return HMC_OK;
+}
+
+// Run CG on all active systems in precision R until every system is done,
+// replaying a captured graph of `chunk` iterations.
+template <typename R>
+static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>* b, V2<R>* x, V2<R>* r,
+                             V2<R>* p, V2<R>* u, int maxit, int nactive, long long* iters_launched) {
+  HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * w.nsys, s));
+  HMC_CUDA(c, cudaMemsetAsync(w.ndone, 0, sizeof(unsigned), s));
+  kb_init<R><<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.st, w.tol2, b, x, r, p, maxit, w.partials,
+                                             w.tickets);
+  HMC_CUDA(c, cudaGetLastError());
+  // systems already done at init (inactive, or converged at start) never pass
+  // through kb_cg_m: count them from the states
+  HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s));
+  HMC_CUDA(c, cudaStreamSynchronize(s));
+  int pre_done = 0;
+  for (int i = 0; i < w.nsys; ++i) pre_done += w.st_host[i].cg.done != CG_RUNNING;
+  if (pre_done == w.nsys) return HMC_OK;
+  const int chunk = 8;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  HMC_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < chunk; ++i) cg_iteration<R>(w, s, x, r, p, u);
+  HMC_CUDA(c, cudaStreamEndCapture(s, &graph));
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  hmc_status status = HMC_OK;
+  long long launched = 0;
+  const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
+  const double bytes_iter = sizeof(R) == 8 ? 192.0 : 96.0;
+  std::vector<char> running(w.nsys);
+  for (int i = 0; i < w.nsys; ++i) running[i] = w.st_host[i].cg.done == CG_RUNNING;
+  for (;;) {
+    double act = 0.0;
+    for (int i = 0; i < w.nsys; ++i) act += running[i] ? (double)w.hsys[i].g.N : 0.0;
+    c->prof.bytes[kid] += act * bytes_iter * chunk;
+    cudaEvent_t a = nullptr;
+    prof_begin(c, kid, &a);
+    e = cudaGraphLaunch(exec, s);
+    prof_end(c, kid, a);
+    c->prof.launches[kid] += 3 * chunk - 1;
+    if (e != cudaSuccess) {
+      status = cuda_fail(c, e, "cudaGraphLaunch");
+      break;
+    }
+    launched += chunk;
+    e = cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      status = cuda_fail(c, e, "batched CG check");
+      break;
+    }
+    int ndone = 0;
+    for (int i = 0; i < w.nsys; ++i) {
+      running[i] = w.st_host[i].cg.done == CG_RUNNING;
+      ndone += !running[i];
+    }
+    if (ndone >= w.nsys) break;
+    if (launched > (long long)maxit + chunk) break;  // every system stops at maxit on the device
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  *iters_launched += launched;
+  (void)nactive;
+  return status;
+}
+
+}  // namespace hmc
 
 using namespace hmc;
 
 extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* sys, int mixed,
                                         hmc_solve_info* infos) {
-  (void)nsys; (void)sys; (void)mixed; (void)infos;
-  return fail(c, HMC_ERR_INVALID, "hmc_solve_batched is not available in this build");
+  if (!c) return HMC_ERR_INVALID;
+  if (nsys < 1 || !sys) return fail(c, HMC_ERR_INVALID, "nsys must be >= 1 and sys non-NULL");
+  if (mixed != 0 && mixed != 1) return fail(c, HMC_ERR_INVALID, "mixed must be 0 or 1");
+  BatchWs w;
+  w.nsys = nsys;
+  w.hsys.resize(nsys);
+  long long off = 0;
+  int maxit = 1;
+  for (int s = 0; s < nsys; ++s) {
+    const hmc_system& y = sys[s];
+    const hmc_lattice& L = y.lat;
+    if (L.n < 1 || L.m < 1 || L.nt < 2 || !(L.beta > 0.0) || !std::isfinite(L.kappa))
+      return fail(c, HMC_ERR_INVALID, "bad lattice in batched system");
+    const long long N = 2LL * L.n * L.m * L.nt;
+    if (N >= (1LL << 30)) return fail(c, HMC_ERR_INVALID, "batched system too large");
+    if (!y.phi || !y.b || !y.x || ((uintptr_t)y.b) % 16 || ((uintptr_t)y.x) % 16 || ((uintptr_t)y.phi) % 8)
+      return fail(c, HMC_ERR_INVALID, "batched system has a NULL or misaligned pointer");
+    if (!(y.sigma >= 0.0) || !(y.tol > 0.0) || y.maxit < 1 || !std::isfinite(y.ms))
+      return fail(c, HMC_ERR_INVALID, "batched system has bad sigma, tol, maxit or mass");
+    const double delta = L.beta / L.nt;
+    if (1.0 - delta * y.ms == 0.0) return fail(c, HMC_ERR_INVALID, "1 - delta*m_s == 0 in batched system");
+    BSys& S = w.hsys[s];
+    S.g = make_geo(L.n, L.m, L.nt, delta, L.kappa);
+    S.off = off;
+    S.dm = delta * y.ms;
+    S.sigma = y.sigma;
+    S.phi = y.phi;
+    S.maxit = y.maxit;
+    off += N;
+    maxit = std::max(maxit, y.maxit);
+  }
+  w.Ntot = off;
+  if (infos) std::memset(infos, 0, sizeof(hmc_solve_info) * nsys);
+
+  // the work runs on a private non-default stream (graph capture needs one),
+  // ordered after and before the context's stream by events
+  cudaStream_t s;
+  HMC_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t ev_in, ev_out;
+  HMC_CUDA(c, cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+  HMC_CUDA(c, cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  HMC_CUDA(c, cudaEventRecord(ev_in, c->stream));
+  HMC_CUDA(c, cudaStreamWaitEvent(s, ev_in, 0));
+  cudaStream_t saved = c->stream;
+  c->stream = s;
+
+  auto body = [&]() -> hmc_status {
+    const size_t Nt = (size_t)w.Ntot;
+    // block tables sized for the smallest block shape (most blocks)
+    plan_blocks(w, 128, 1);
+    const int max_blocks = w.blocks;
+    w.hbsys.reserve(max_blocks);
+    HMC_TRY(bmalloc(c, w, (void**)&w.sys, sizeof(BSys) * nsys));
+    HMC_TRY(bmalloc(c, w, (void**)&w.bsys, sizeof(int) * max_blocks));
+    HMC_TRY(bmalloc(c, w, (void**)&w.st, sizeof(BState) * nsys));
+    HMC_TRY(bmalloc(c, w, (void**)&w.tol2, sizeof(double) * nsys));
+    HMC_TRY(bmalloc(c, w, (void**)&w.rrbb, sizeof(double) * 2 * nsys));
+    HMC_TRY(bmalloc(c, w, (void**)&w.tickets, sizeof(unsigned) * nsys));
+    HMC_TRY(bmalloc(c, w, (void**)&w.ndone, sizeof(unsigned)));
+    HMC_TRY(bmalloc(c, w, (void**)&w.partials, sizeof(double) * 2 * max_blocks));
+    HMC_TRY(bmalloc(c, w, (void**)&w.E, sizeof(double2) * Nt));
+    HMC_TRY(bmalloc(c, w, (void**)&w.phi32, sizeof(float) * Nt));
+    HMC_TRY(bmalloc(c, w, (void**)&w.x, sizeof(double2) * Nt));
+    HMC_TRY(bmalloc(c, w, (void**)&w.b, sizeof(double2) * Nt));
+    HMC_TRY(bmalloc(c, w, (void**)&w.r, sizeof(double2) * Nt));
+    if (!mixed) {
+      HMC_TRY(bmalloc(c, w, (void**)&w.p, sizeof(double2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.u, sizeof(double2) * Nt));
+    } else {
+      HMC_TRY(bmalloc(c, w, (void**)&w.u, sizeof(double2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.r32, sizeof(float2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.e32, sizeof(float2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.p32v, sizeof(float2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.u32, sizeof(float2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.rr32, sizeof(float2) * Nt));
+    }
+    HMC_CUDA(c, cudaMallocHost(&w.st_host, sizeof(BState) * nsys));
+    HMC_CUDA(c, cudaMallocHost(&w.rrbb_host, sizeof(double) * 2 * nsys));
+    HMC_CUDA(c, cudaMallocHost(&w.ndone_host, sizeof(unsigned)));
+    HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * nsys, s));
+    // gather b, phases
+    for (int i = 0; i < nsys; ++i)
+      HMC_CUDA(c, cudaMemcpyAsync(w.b + w.hsys[i].off, sys[i].b, sizeof(double2) * w.hsys[i].g.N,
+                                  cudaMemcpyDeviceToDevice, s));
+    plan_blocks(w, 256, 2);
+    HMC_TRY(upload_plan<double>(c, w, s));
+    kb_phase<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.E, w.phi32);
+    HMC_CUDA(c, cudaGetLastError());
+    c->prof.launches[K_BATCH_MISC]++;
+
+    std::vector<double> tol2(nsys);
+    std::vector<BState> init(nsys);
+    for (int i = 0; i < nsys; ++i) {
+      std::memset(&init[i], 0, sizeof(BState));
+      init[i].active = 1;
+    }
+    HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
+    std::vector<int> iters(nsys, 0), outer(nsys, 0), inner(nsys, 0), status(nsys, HMC_OK);
+    std::vector<double> rel(nsys, 0.0);
+    long long launched = 0;
+    int threads = 256, ipt = 2;
+
+    if (!mixed) {
+      for (int i = 0; i < nsys; ++i) tol2[i] = sys[i].tol * sys[i].tol;
+      HMC_CUDA(c, cudaMemcpyAsync(w.tol2, tol2.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s));
+      HMC_TRY(autotune<double>(c, w, s, w.x, w.r, w.p, w.u, w.b, &threads, &ipt));
+      plan_blocks(w, threads, ipt);
+      HMC_TRY(upload_plan<double>(c, w, s));
+      HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
+      HMC_TRY(batched_cg<double>(c, w, s, w.b, w.x, w.r, w.p, w.u, maxit, nsys, &launched));
+      HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s));
+      HMC_CUDA(c, cudaStreamSynchronize(s));
+      for (int i = 0; i < nsys; ++i) {
+        iters[i] = w.st_host[i].cg.iter;
+        if (w.st_host[i].cg.done == CG_MAXIT || w.st_host[i].cg.iter > sys[i].maxit) status[i] = HMC_ERR_NOT_CONVERGED;
+        if (w.st_host[i].cg.done == CG_BREAKDOWN) status[i] = HMC_ERR_NAN;
+      }
+    } else {
+      // defect correction: x = 0, r = b; loop: solve A e = r in FP32, x += e,
+      // r = b - A x in FP64
+      HMC_CUDA(c, cudaMemsetAsync(w.x, 0, sizeof(double2) * Nt, s));
+      std::vector<double> bnorm(nsys, 0.0), rnorm(nsys, 0.0);
+      std::vector<int> done(nsys, 0);
+      bool tuned = false;
+      const int max_outer = 50;
+      for (int it = 0; it <= max_outer; ++it) {
+        // r = b - A x (FP64), r32 = r
+        kb_mdag64<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.E, w.x, w.u);
+        kb_resid64<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.E, w.u, w.x, w.b, w.r, w.r32, w.rrbb,
+                                                  w.partials, w.tickets);
+        HMC_CUDA(c, cudaGetLastError());
+        c->prof.launches[K_BATCH_RESID] += 2;
+        HMC_CUDA(c, cudaMemcpyAsync(w.rrbb_host, w.rrbb, sizeof(double) * 2 * nsys, cudaMemcpyDeviceToHost, s));
+        HMC_CUDA(c, cudaStreamSynchronize(s));
+        int nact = 0;
+        for (int i = 0; i < nsys; ++i) {
+          bnorm[i] = std::sqrt(w.rrbb_host[2 * i + 1]);
+          rnorm[i] = std::sqrt(w.rrbb_host[2 * i]);
+          rel[i] = bnorm[i] > 0 ? rnorm[i] / bnorm[i] : 0.0;
+          if (!std::isfinite(rnorm[i])) {
+            status[i] = HMC_ERR_NAN;
+            done[i] = 1;
+          }
+          if (!done[i] && rnorm[i] <= sys[i].tol * bnorm[i]) done[i] = 1;
+          if (!done[i] && outer[i] >= max_outer) {
+            status[i] = HMC_ERR_NOT_CONVERGED;
+            done[i] = 1;
+          }
+          init[i].active = done[i] ? 0 : 1;
+          // inner tolerance: what is left to gain, with margin, floored at FP32 reach
+          const double need = bnorm[i] > 0 ? sys[i].tol * bnorm[i] / std::max(rnorm[i], 1e-300) : 1.0;
+          const double t = std::max(0.5 * need, 1e-6);
+          tol2[i] = t * t;
+          nact += init[i].active;
+        }
+        if (nact == 0) break;
+        HMC_CUDA(c, cudaMemcpyAsync(w.tol2, tol2.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s));
+        HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
+        if (!tuned) {
+          // r32 now holds the first right-hand sides: tune the FP32 block shape on them
+          HMC_TRY(autotune<float>(c, w, s, w.e32, w.rr32, w.p32v, w.u32, w.r32, &threads, &ipt));
+          plan_blocks(w, threads, ipt);
+          HMC_TRY(upload_plan<float>(c, w, s));
+          HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
+          tuned = true;
+        }
+        HMC_TRY(batched_cg<float>(c, w, s, w.r32, w.e32, w.rr32, w.p32v, w.u32, 2000, nact, &launched));
+        HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s));
+        HMC_CUDA(c, cudaStreamSynchronize(s));
+        for (int i = 0; i < nsys; ++i) {
+          if (!init[i].active) continue;
+          inner[i] += w.st_host[i].cg.iter;
+          outer[i] += 1;
+        }
+        kb_xadd<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.st, w.e32, w.x);
+        HMC_CUDA(c, cudaGetLastError());
+        c->prof.launches[K_BATCH_MISC]++;
+      }
+      for (int i = 0; i < nsys; ++i) iters[i] = outer[i];
+    }
+    // true residuals in FP64 (also the report for the FP64 path), scatter x
+    kb_mdag64<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.E, w.x, w.u);
+    kb_resid64<<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.E, w.u, w.x, w.b, w.r, nullptr, w.rrbb,
+                                              w.partials, w.tickets);
+    HMC_CUDA(c, cudaGetLastError());
+    c->prof.launches[K_BATCH_RESID] += 2;
+    HMC_CUDA(c, cudaMemcpyAsync(w.rrbb_host, w.rrbb, sizeof(double) * 2 * nsys, cudaMemcpyDeviceToHost, s));
+    for (int i = 0; i < nsys; ++i)
+      HMC_CUDA(c, cudaMemcpyAsync(sys[i].x, w.x + w.hsys[i].off, sizeof(double2) * w.hsys[i].g.N,
+                                  cudaMemcpyDeviceToDevice, s));
+    HMC_CUDA(c, cudaStreamSynchronize(s));
+    hmc_status worst = HMC_OK;
+    for (int i = 0; i < nsys; ++i) {
+      const double bb = w.rrbb_host[2 * i + 1];
+      rel[i] = bb > 0 ? std::sqrt(w.rrbb_host[2 * i] / bb) : 0.0;
+      if (status[i] == HMC_OK && !(rel[i] <= sys[i].tol * (mixed ? 1.0 : 1.0 + 1e-6)) && mixed)
+        status[i] = HMC_ERR_NOT_CONVERGED;
+      if (status[i] != HMC_OK && worst == HMC_OK) worst = (hmc_status)status[i];
+      if (infos) {
+        infos[i].iters = mixed ? inner[i] : iters[i];
+        infos[i].iters_outer = mixed ? outer[i] : 0;
+        infos[i].iters_inner = mixed ? inner[i] : 0;
+        infos[i].status = status[i];
+        infos[i].true_rel_res = rel[i];
+        infos[i].applies64 = mixed ? outer[i] + 1 : iters[i];
+        infos[i].applies32 = mixed ? inner[i] : 0;
+        const double N = (double)w.hsys[i].g.N;
+        infos[i].bytes = (long long)(N * (192.0 * infos[i].applies64 + 96.0 * infos[i].applies32));
+      }
+    }
+    if (worst != HMC_OK) return fail(c, worst, "a batched system did not converge");
+    return HMC_OK;
+  };
+  hmc_status st = body();
+  cudaStreamSynchronize(s);
+  c->stream = saved;
+  cudaEventRecord(ev_out, s);
+  cudaStreamWaitEvent(saved, ev_out, 0);
+  cudaEventDestroy(ev_in);
+  cudaEventDestroy(ev_out);
+  bfree(w);
+  cudaStreamDestroy(s);
+  return st;
 }

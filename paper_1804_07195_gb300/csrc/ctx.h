@@ -37,9 +37,9 @@ enum KernelId {
   K_FORCE,
   K_AXPY,
   K_MD,
-  K_BATCH_MDAG,
-  K_BATCH_M,
-  K_BATCH_P,
+  K_BATCH_CG64,
+  K_BATCH_CG32,
+  K_BATCH_INIT,
   K_BATCH_RESID,
   K_BATCH_MISC,
   K_COUNT

@@ -12,8 +12,8 @@ const char* const kKernelNames[K_COUNT] = {
     "cg_Mdag_f64",    "cg_M_update_f64", "cg_p_f64",     "cg_Mdag_f32",    "cg_M_update_f32",
     "cg_p_f32",       "residual_f64",   "residual_f32",  "cg_init0",       "convert",
     "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
-    "force",          "axpy",           "md_update",     "batch_Mdag",     "batch_M_update",
-    "batch_p",        "batch_residual", "batch_misc"};
+    "force",          "axpy",           "md_update",     "batch_cg_graph_f64", "batch_cg_graph_f32",
+    "batch_init",     "batch_residual", "batch_misc"};
 
 const double kKernelBytesPerSite[K_COUNT] = {
     8 + 16 + 4,          // phase: phi in, E and phi32 out
@@ -39,7 +39,7 @@ const double kKernelBytesPerSite[K_COUNT] = {
     16 + 16 + 16 + 16 + 16,  // force: eta, E, xi, chi, grad rw
     24,                  // axpy
     24,                  // md update
-    16 + 16 + 16, 16 + 16 + 16 + 32 + 32, 16 + 32, 16 * 5, 0};
+    192, 96, 16 * 4, 16 * 5, 0};
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restrict__ phi,

@@ -87,7 +87,8 @@ def test_fgmres_iteration_structure_matches_oracle():
     with ctx_for(w.lat) as ctx:
         _, info = ctx.solve_fgmres(dev(w.phi), 0.0, dev(w.b), tol=1e-10)
     assert abs(info["iters_outer"] - ref.outer_iters) <= 1, (info, ref.outer_iters)
-    assert abs(info["iters"] - ref.iters) <= 3 + 2 * abs(info["iters_outer"] - ref.outer_iters), (info, ref.iters)
+    # an extra restart on one side adds up to m = 10 Arnoldi steps
+    assert abs(info["iters"] - ref.iters) <= 3 + 10 * abs(info["iters_outer"] - ref.outer_iters), (info, ref.iters)
     assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters, (info, ref.inner_iters)
 
 

@@ -160,8 +160,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--kernel-case", default=None,
+                    choices=["spcg", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    help="run one solve or application on the benchmark lattice and exit "
+                         "(the small case for kernel profiles)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
+    if args.kernel_case:
+        kernel_case(args.kernel_case)
+        return
 
     if args.impl == "reference":
         run_reference(args, rank)
@@ -367,6 +374,50 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def kernel_case(case):
+    """One solve (or 20 operator applications) on the 102x102x64 lattice: the
+    case the ncu kernel profiles are taken on."""
+    import torch
+    import paper_1804_07195_gb300 as hmc
+    from paper_1804_07195_gb300 import build
+    import workloads as W
+    build.build()
+    if case == "batched":
+        sys_ = []
+        for w in W.c4_instances():
+            p = w.lat
+            lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+            for ms, b in zip(w.masses, w.rho):
+                sys_.append({"lattice": lat, "phi": torch.tensor(w.phi, device="cuda"), "ms": ms,
+                             "b": torch.tensor(b, device="cuda"),
+                             "x": torch.zeros(p.nsites, dtype=torch.complex128, device="cuda")})
+        with hmc.Context(sys_[0]["lattice"]) as ctx:
+            infos = ctx.solve_batched(sys_, mixed=True)
+        print(json.dumps({"case": case, "systems": len(infos),
+                          "max_true_rel_res": max(i["true_rel_res"] for i in infos)}))
+        return
+    w = W.workload("C5")
+    p = w.lat
+    lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+    phi = torch.tensor(w.phi, device="cuda")
+    b = torch.tensor(w.b, device="cuda")
+    with hmc.Context(lat) as ctx:
+        if case == "spcg":
+            _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
+        elif case == "cg64":
+            _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)
+        elif case == "fgmres":
+            _, info = ctx.solve_fgmres(phi, 0.0, b, tol=1e-10)
+        else:
+            x = b.to(torch.complex64) if case == "mmdag32" else b
+            ctx.load_field(phi)
+            for _ in range(20):
+                y = ctx.apply_MMdag(None, 0.0, x)
+            info = {"applications": 20}
+        torch.cuda.synchronize()
+    print(json.dumps({"case": case, **{k: v for k, v in info.items()}}))
 
 
 def kernel_source_sha():

@@ -1,5 +1,6 @@
 // C ABI entry points of libhmc: context management, argument validation,
 // operator applications, solves and instrumentation.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -168,7 +169,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   c->ws_bytes[WS_E] = N * sizeof(double2);
   if ((e = cudaMalloc(&c->ws[WS_PHI32], N * sizeof(float))) != cudaSuccess) return bail(e);
   c->ws_bytes[WS_PHI32] = N * sizeof(float);
-  if ((e = cudaMalloc(&c->partials, sizeof(double) * kMaxRed * c->max_grid)) != cudaSuccess) return bail(e);
+  const size_t npart = (size_t)kMaxRed * std::max(c->max_grid, c->nsm * kOneItemBlocksPerSM);
+  if ((e = cudaMalloc(&c->partials, sizeof(double) * npart)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->tickets, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);

@@ -55,7 +55,7 @@ enum WsSlot {
   WS_U64,        // M^dagger intermediate, complex128
   WS_U32,
   WS_CG_R64, WS_CG_P64, WS_CG_X64,
-  WS_CG_R32, WS_CG_P32, WS_CG_X32, WS_CG_B32,
+  WS_CG_R32, WS_CG_P32, WS_CG_X32, WS_CG_B32, WS_CG_Q32,
   WS_FG_R, WS_FG_W, WS_FG_X, WS_FG_V, WS_FG_Z,  // FGMRES vectors; V, Z hold `restart` each
   WS_F_ETA, WS_F_XI, WS_F_SRC, WS_F_TMP,        // force / action temporaries
   WS_MD_CHI, WS_MD_GRAD, WS_MD_FORCE,           // trajectory: pseudofermions, level forces
@@ -110,6 +110,7 @@ namespace hmc {
 
 constexpr int kThreads = 256;
 constexpr int kMaxGridPerSM = 8;
+constexpr int kOneItemBlocksPerSM = 64;
 constexpr int kMaxRed = 40;  // values reduced at once at most
 constexpr int kTickets = 16;
 
@@ -137,6 +138,16 @@ hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out);
 inline int grid_for(const hmc_ctx* c, long long work) {
   long long g = (work + kThreads - 1) / kThreads;
   if (g > c->max_grid) g = c->max_grid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Grid with one thread per work item (up to a cap), for kernels whose loop
+// should run once per thread so the block scheduler balances the load.
+inline int grid_one(const hmc_ctx* c, long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  const long long cap = (long long)c->nsm * kOneItemBlocksPerSM;
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }

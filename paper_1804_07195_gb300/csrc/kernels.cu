@@ -9,7 +9,7 @@ namespace hmc {
 // arrays it must touch, each once), used to report achieved bandwidth.
 const char* const kKernelNames[K_COUNT] = {
     "phase_table",    "apply_Mdag_f64", "apply_M_f64",   "apply_Mdag_f32", "apply_M_f32",
-    "cg_Mdag_f64",    "cg_M_update_f64", "cg_p_f64",     "cg_Mdag_f32",    "cg_M_update_f32",
+    "cg_Mdag_f64",    "cg_M_update_f64", "cg_p_f64",     "cg_pMdag_f32",    "cg_M_update_f32",
     "cg_p_f32",       "residual_f64",   "residual_f32",  "cg_init0",       "convert",
     "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
     "force",          "axpy",           "md_update",     "batch_cg_graph_f64", "batch_cg_graph_f32",
@@ -24,7 +24,7 @@ const double kKernelBytesPerSite[K_COUNT] = {
     16 + 16 + 16,        // cg M^dagger f64: p, E, u
     16 + 16 + 16 + 32 + 32,  // cg M f64: u, E, p, x rw, r rw
     16 + 32,             // p = r + beta p
-    8 + 4 + 8,           // cg M^dagger f32
+    8 + 8 + 4 + 8 + 8,   // cg M^dagger f32 with the p update: r, p_old, phi32, p_new, u
     8 + 4 + 8 + 16 + 16, // cg M f32
     8 + 16,              // p f32
     16 + 16 + 16 + 16 + 16,  // residual f64: u, E, x, b, r
@@ -187,6 +187,106 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(int N, const V2<R>* __restric
   }
 }
 
+// FP32 CG with the direction update folded into the M^dagger kernel. With
+// p_new = r + beta p_old evaluated at every stencil point it reads (double
+// buffered: p_old and p_new are different arrays):
+//   u = M^dagger p_new,  pAp = |u|^2 + sigma |p_new|^2,  alpha = rr / pAp,
+// and p_new is stored at the thread's own sites. beta = 0 on the first
+// iteration (the init kernels set p_old = r, so no NaN can enter).
+__global__ void __launch_bounds__(kThreads) k_cg32_pmdag(Geo g, Phase<float> ph, float dm,
+                                                         const float2* __restrict__ r,
+                                                         const float2* __restrict__ pold,
+                                                         float2* __restrict__ pnew,
+                                                         float2* __restrict__ u, CGScal* sc,
+                                                         double* partials, unsigned* ticket) {
+  if (sc->done) return;
+  const float sigma = (float)sc->sigma;
+  const float beta = (float)sc->beta;
+  const int H = g.H;
+  const float dk = (float)g.dk;
+  float loc = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    auto P = [&](int k) {
+      float2 a = r[k], b = pold[k];
+      return Cx<float>{fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y)};
+    };
+    Cx<float> pa = P(nb.q), pb = P(H + nb.q);
+    st(pnew, nb.q, pa);
+    st(pnew, H + nb.q, pb);
+    Cx<float> ea = ph(nb.tp);
+    Cx<float> za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, nb.wrap_tp);
+    Cx<float> ta = cfma(za, P(nb.tp), Cx<float>{-pa.re, -pa.im});
+    Cx<float> oa = hopsum(ta, dk, pb, P(H + nb.im1), P(H + nb.jm1));
+    Cx<float> eb = ph(H + nb.tm);
+    Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, nb.wrap_tm);
+    Cx<float> tb = cfma(zb, P(H + nb.tm), pb);
+    Cx<float> ob = hopsum(tb, dk, pa, P(nb.ip1), P(nb.jp1));
+    st(u, nb.q, oa);
+    st(u, H + nb.q, ob);
+    loc += norm2(oa) + norm2(ob);
+    if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+  }
+  double acc[1] = {(double)loc};
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    sc->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      sc->alpha = 0.0;
+      sc->done = CG_BREAKDOWN;
+    } else {
+      sc->alpha = sc->rr / pAp;
+    }
+  }
+}
+
+// A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2
+// (FP32 vectors; one float partial per thread, reduced in FP64).
+__global__ void __launch_bounds__(kThreads) k_cg32_m(Geo g, Phase<float> ph, float dm,
+                                                     const float2* __restrict__ u,
+                                                     const float2* __restrict__ p,
+                                                     float2* __restrict__ x, float2* __restrict__ r,
+                                                     CGScal* sc, double* partials, unsigned* ticket) {
+  if (sc->done) return;
+  const float sigma = (float)sc->sigma;
+  const float alpha = (float)sc->alpha;
+  float loc = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
+    Nbr nb = neighbours(g, q);
+    PairOut<float> o = m_pair<float>(g, ph, dm, u, nb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = h ? g.H + q : q;
+      Cx<float> Ap = h ? o.b : o.a;
+      float2 pk = p[k], xk = x[k], rk = r[k];
+      Ap.re = fmaf(sigma, pk.x, Ap.re);
+      Ap.im = fmaf(sigma, pk.y, Ap.im);
+      xk.x = fmaf(alpha, pk.x, xk.x);
+      xk.y = fmaf(alpha, pk.y, xk.y);
+      rk.x = fmaf(-alpha, Ap.re, rk.x);
+      rk.y = fmaf(-alpha, Ap.im, rk.y);
+      x[k] = xk;
+      r[k] = rk;
+      loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
+    }
+  }
+  double acc[1] = {(double)loc};
+  double tot[1];
+  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+    double rr = tot[0];
+    sc->beta = rr / sc->rr;
+    sc->rr = rr;
+    sc->iter += 1;
+    if (!isfinite(rr))
+      sc->done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      sc->done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      sc->done = CG_MAXIT;
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
                                                     const V2<R>* __restrict__ u,
@@ -300,11 +400,11 @@ __global__ void __launch_bounds__(kThreads) k_redot(int N, const double2* __rest
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-// h[i] = V_i^H w for i < NV (compile-time upper bound on nv).
+// h[i] = V_i^H w for the NV basis vectors (NV a compile-time constant, so the
+// basis pointers stay in the parameter bank and every loop unrolls).
 template <int NV>
-__global__ void __launch_bounds__(kThreads) k_mdot(int N, VecList V, int nv,
-                                                   const double2* __restrict__ w, double* hout,
-                                                   double* partials, unsigned* ticket) {
+__global__ void __launch_bounds__(kThreads) k_mdot(int N, VecList V, const double2* __restrict__ w,
+                                                   double* hout, double* partials, unsigned* ticket) {
   double acc[2 * NV];
 #pragma unroll
   for (int i = 0; i < 2 * NV; ++i) acc[i] = 0.0;
@@ -312,30 +412,32 @@ __global__ void __launch_bounds__(kThreads) k_mdot(int N, VecList V, int nv,
     double2 wk = w[k];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      if (i < nv) {
-        double2 vk = V.v[i][k];
-        // conj(v) w
-        acc[2 * i] = fma(vk.x, wk.x, fma(vk.y, wk.y, acc[2 * i]));
-        acc[2 * i + 1] = fma(vk.x, wk.y, fma(-vk.y, wk.x, acc[2 * i + 1]));
-      }
+      double2 vk = V.v[i][k];
+      // conj(v) w
+      acc[2 * i] = fma(vk.x, wk.x, fma(vk.y, wk.y, acc[2 * i]));
+      acc[2 * i + 1] = fma(vk.x, wk.y, fma(-vk.y, wk.x, acc[2 * i + 1]));
     }
   }
   double tot[2 * NV];
   if (grid_sum<2 * NV>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-    for (int i = 0; i < 2 * nv; ++i) hout[i] = tot[i];
+#pragma unroll
+    for (int i = 0; i < 2 * NV; ++i) hout[i] = tot[i];
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_gsupd(int N, VecList V, int nv, const double* h,
+// w -= sum_i h[i] V_i over the NV basis vectors, then |w|^2.
+template <int NV>
+__global__ void __launch_bounds__(kThreads) k_gsupd(int N, VecList V, const double* h,
                                                     double2* __restrict__ w, double* ww,
                                                     double* partials, unsigned* ticket) {
-  __shared__ double hs[2 * kMaxRestart];
-  if (threadIdx.x < 2 * nv) hs[threadIdx.x] = h[threadIdx.x];
+  __shared__ double hs[2 * NV];
+  if (threadIdx.x < 2 * NV) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
   double acc[1] = {0.0};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     double2 wk = w[k];
-    for (int i = 0; i < nv; ++i) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
       double2 vk = V.v[i][k];
       const double hr = hs[2 * i], hi = hs[2 * i + 1];
       // w -= h v
@@ -452,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __res
 
 // ---------------------------------------------------------------------------
 // Launchers
-#define GRID(work) grid_for(c, (work)), kThreads, 0, c->stream
+#define GRID(work) grid_one(c, (work)), kThreads, 0, c->stream
 
 hmc_status k_phase_launch(hmc_ctx* c, const double* phi) {
   const int N = c->geo.N;
@@ -526,6 +628,21 @@ INST(float)
 INST(double)
 #undef INST
 
+hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, float dm, const float2* r, const float2* pold,
+                             float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
+  return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
+    k_cg32_pmdag<<<grid_one(c, g.H), kThreads, 0, c->stream>>>(g, phase_of<float>(c), dm, r, pold, pnew,
+                                                              u, sc, c->partials, ticket);
+  });
+}
+hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, float dm, const float2* u, const float2* p, float2* x,
+                         float2* r, CGScal* sc, unsigned* ticket) {
+  return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
+    k_cg32_m<<<grid_one(c, g.H), kThreads, 0, c->stream>>>(g, phase_of<float>(c), dm, u, p, x, r, sc,
+                                                          c->partials, ticket);
+  });
+}
+
 hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out) {
   return launch(c, K_CONVERT, [&] { k_to32<<<GRID(N)>>>(N, in, out); });
 }
@@ -539,21 +656,31 @@ hmc_status redot_launch(hmc_ctx* c, int N, const double2* u, const double2* v, d
                         unsigned* ticket) {
   return launch(c, K_NORM, [&] { k_redot<<<GRID(N)>>>(N, u, v, out, c->partials, ticket); });
 }
+#define NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
 hmc_status mdot_launch(hmc_ctx* c, int N, VecList V, int nv, const double2* w, double* hout,
                        unsigned* ticket) {
+  if (nv < 1 || nv > kMaxRestart) return fail(c, HMC_ERR_INVALID, "basis size out of range");
   return launch_b(c, K_MDOT, 16.0 * N * (nv + 1), [&] {
-    if (nv <= 4)
-      k_mdot<4><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
-    else if (nv <= 8)
-      k_mdot<8><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
-    else
-      k_mdot<kMaxRestart><<<GRID(N)>>>(N, V, nv, w, hout, c->partials, ticket);
+    switch (nv) {
+#define X(n) \
+  case n: k_mdot<n><<<GRID(N)>>>(N, V, w, hout, c->partials, ticket); break;
+      NV_CASES(X)
+#undef X
+    }
   });
 }
 hmc_status gsupd_launch(hmc_ctx* c, int N, VecList V, int nv, const double* h, double2* w,
                         double* ww, unsigned* ticket) {
-  return launch_b(c, K_GSUPD, 16.0 * N * (nv + 2),
-                [&] { k_gsupd<<<GRID(N)>>>(N, V, nv, h, w, ww, c->partials, ticket); });
+  if (nv < 1 || nv > kMaxRestart) return fail(c, HMC_ERR_INVALID, "basis size out of range");
+  return launch_b(c, K_GSUPD, 16.0 * N * (nv + 2), [&] {
+    switch (nv) {
+#define X(n) \
+  case n: k_gsupd<n><<<GRID(N)>>>(N, V, h, w, ww, c->partials, ticket); break;
+      NV_CASES(X)
+#undef X
+    }
+  });
 }
 hmc_status scale_launch(hmc_ctx* c, int N, double s, const double2* w, double2* v, float2* v32) {
   return launch(c, K_SCALE, [&] { k_scale<<<GRID(N)>>>(N, s, w, v, v32); });

@@ -29,6 +29,14 @@ hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<
 template <typename R>
 hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc);
 
+// FP32 CG, two kernels per iteration: p_new = r + beta p_old folded into
+// u = M^dagger p_new (with pAp and alpha), then the M kernel with the updates.
+// One cell-time per thread.
+hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, float dm, const float2* r, const float2* pold,
+                             float2* pnew, float2* u, CGScal* sc, unsigned* ticket);
+hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, float dm, const float2* u, const float2* p, float2* x,
+                         float2* r, CGScal* sc, unsigned* ticket);
+
 // r = b - (M u + sigma x), with |r|^2 and |b|^2 reduced. When init != NULL the
 // last block initialises a CG state (rr, bb, thresh = tol2 * bb, iter 0, done if
 // rr <= thresh) and p = r is written. When out2 != NULL it receives {|r|^2, |b|^2}.

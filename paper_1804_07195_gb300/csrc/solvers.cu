@@ -60,13 +60,26 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
     HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, p, sc, tol2, maxit, nullptr, tk));
     if (sizeof(R) == 8) st->applies64++; else st->applies32++;
   }
+  // FP32: two kernels per iteration with a second direction buffer q
+  // (p and q alternate as p_old / p_new); the chunk length stays even so an
+  // iteration count that ends a chunk leaves the newest direction in p.
+  V2<R>* q = nullptr;
+  if (sizeof(R) == 4)
+    HMC_TRY(ws_get(c, WS_CG_Q32, sizeof(V2<R>) * (size_t)g.N, (void**)&q));
   int chunk = 4;
   int launched = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      HMC_TRY(cg_mdag_launch<R>(c, g, dm, p, u, sc, tk));
-      HMC_TRY(cg_m_launch<R>(c, g, dm, u, p, x, r, sc, tk));
-      HMC_TRY(cg_p_launch<R>(c, g.N, r, p, sc));
+      if constexpr (sizeof(R) == 4) {
+        float2* pold = (i & 1) ? (float2*)q : (float2*)p;
+        float2* pnew = (i & 1) ? (float2*)p : (float2*)q;
+        HMC_TRY(cg32_pmdag_launch(c, g, (float)dm, (const float2*)r, pold, pnew, (float2*)u, sc, tk));
+        HMC_TRY(cg32_m_launch(c, g, (float)dm, (const float2*)u, pnew, (float2*)x, (float2*)r, sc, tk));
+      } else {
+        HMC_TRY(cg_mdag_launch<R>(c, g, dm, p, u, sc, tk));
+        HMC_TRY(cg_m_launch<R>(c, g, dm, u, p, x, r, sc, tk));
+        HMC_TRY(cg_p_launch<R>(c, g.N, r, p, sc));
+      }
     }
     launched += chunk;
     HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));

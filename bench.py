@@ -302,6 +302,7 @@ def main():
                 "algorithmic_bytes_per_site": bytes_launch / N,
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()
                             if v["launches"]},
+                "tuned_shape": {"threads": dstat["threads"], "waves": dstat["waves"]},
                 "method": "CUDA events around every launch on the context stream, one profiled "
                           "trajectory after the timed region"}
 

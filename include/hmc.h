@@ -261,6 +261,8 @@ typedef struct {
   double ms_total;      /* summed CUDA-event time (0 unless timing was on) */
   double bytes_total;   /* algorithmic HBM bytes summed over those launches: each
                            array the kernel must read or write, counted once */
+  int threads;          /* launch shape chosen by the autotuner (CG kernels) */
+  int waves;            /* grid = waves x resident blocks (0: one item per thread) */
 } hmc_kernel_stat;
 
 /* Per-kernel launch counters are always kept. With timing on, every launch of

@@ -289,7 +289,8 @@ class Context:
         cnt = C.c_int()
         self._check(self.lib.hmc_profile_read(self.h, arr, _abi.HMC_NKERNELS, C.byref(cnt)))
         return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms_total,
-                                       "bytes": arr[i].bytes_total}
+                                       "bytes": arr[i].bytes_total,
+                                       "threads": arr[i].threads, "waves": arr[i].waves}
                 for i in range(cnt.value)}
 
 

@@ -27,6 +27,7 @@ hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out) {
   if (c->ws_bytes[slot] < bytes) {
     if (c->ws[slot]) {
       cudaStreamSynchronize(c->stream);
+      destroy_graphs(c);
       cudaFree(c->ws[slot]);
       c->ws[slot] = nullptr;
       c->ws_bytes[slot] = 0;
@@ -84,6 +85,65 @@ void prof_end(hmc_ctx* c, int id, cudaEvent_t a) {
   cudaEventRecord(b, c->stream);
   c->prof.pending.push_back(Pending{a, b, id});
   if (c->prof.pending.size() > 16384) prof_drain(c, 8192);
+}
+
+hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cudaGraphExec_t* out) {
+  *out = nullptr;
+  if (!c->cap_stream) HMC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = c->stream;
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  hmc_status st = e == cudaSuccess ? body() : cuda_fail(c, e, "cudaStreamBeginCapture");
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) {
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e2 != cudaSuccess && st == HMC_OK) st = cuda_fail(c, e2, "cudaStreamEndCapture");
+  }
+  c->capturing = false;
+  c->stream = saved;
+  if (st == HMC_OK && graph) {
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return st;
+}
+
+GraphEntry* find_graph(hmc_ctx* c, int kind, const void* const key[6]) {
+  for (auto& g : c->graphs) {
+    if (g.kind != kind) continue;
+    bool same = true;
+    for (int i = 0; i < 6; ++i) same = same && g.key[i] == key[i];
+    if (same) {
+      g.last_use = ++c->graph_clock;
+      return &g;
+    }
+  }
+  return nullptr;
+}
+
+GraphEntry* add_graph(hmc_ctx* c, int kind, const void* const key[6], cudaGraphExec_t exec) {
+  constexpr size_t kMaxGraphs = 16;
+  if (c->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+    size_t old = 0;
+    for (size_t i = 1; i < c->graphs.size(); ++i)
+      if (c->graphs[i].last_use < c->graphs[old].last_use) old = i;
+    cudaGraphExecDestroy(c->graphs[old].exec);
+    c->graphs.erase(c->graphs.begin() + old);
+  }
+  GraphEntry g;
+  g.kind = kind;
+  for (int i = 0; i < 6; ++i) g.key[i] = key[i];
+  g.exec = exec;
+  g.last_use = ++c->graph_clock;
+  c->graphs.push_back(g);
+  return &c->graphs.back();
+}
+
+void destroy_graphs(hmc_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
 }
 
 hmc_status prepare_field(hmc_ctx* c, const double* phi) {
@@ -164,6 +224,7 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) return bail(e);
   c->max_grid = c->nsm * kMaxGridPerSM;
+  for (int k = 0; k < K_COUNT; ++k) c->shape[k] = Shape{};
   const size_t N = (size_t)c->geo.N;
   if ((e = cudaMalloc(&c->ws[WS_E], N * sizeof(double2))) != cudaSuccess) return bail(e);
   c->ws_bytes[WS_E] = N * sizeof(double2);
@@ -175,6 +236,10 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->sc, 0, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
+  // one-item grids of the tuned kernels may reach nsm * 128 blocks of 128 threads
+  if ((e = cudaFree(c->partials)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->partials, sizeof(double) * kMaxRed * c->nsm * 2 * kOneItemBlocksPerSM)) != cudaSuccess)
+    return bail(e);
   if ((e = cudaMallocHost(&c->sc_host, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->dscal, sizeof(double) * 64)) != cudaSuccess) return bail(e);
   if ((e = cudaMallocHost(&c->dscal_host, sizeof(double) * 64)) != cudaSuccess) return bail(e);
@@ -185,6 +250,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
 hmc_status hmc_destroy(hmc_ctx* c) {
   if (!c) return HMC_ERR_INVALID;
   if (c->stream || c->device >= 0) cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int i = 0; i < WS_COUNT; ++i)
     if (c->ws[i]) cudaFree(c->ws[i]);
   if (c->partials) cudaFree(c->partials);
@@ -360,6 +427,8 @@ hmc_status hmc_profile_read(hmc_ctx* c, hmc_kernel_stat* out, int max, int* coun
     out[n].launches = c->prof.launches[i];
     out[n].ms_total = c->prof.ms[i];
     out[n].bytes_total = c->prof.bytes[i];
+    out[n].threads = c->shape[i].threads;
+    out[n].waves = c->shape[i].waves;
     ++n;
   }
   *count = n;

@@ -217,6 +217,7 @@ struct CGScal {
   double bb;     // |b|^2
   double thresh; // stop when rr <= thresh (= tol^2 |b|^2)
   double sigma;  // shift of the operator
+  double dm;     // delta * m_s of the operator (read by the iteration kernels)
   int iter, maxit;
   int done;      // 0 running, 1 converged, 2 iteration limit, 3 breakdown (pAp <= 0 / NaN)
   int pad;

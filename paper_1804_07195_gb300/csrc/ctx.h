@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,22 @@ struct Pending {
   int id;
 };
 
+// A captured chunk of solver iterations, keyed by the buffers it touches.
+struct GraphEntry {
+  int kind = 0;
+  const void* key[6] = {};
+  cudaGraphExec_t exec = nullptr;
+  long long last_use = 0;
+};
+
+// Launch shape of a tuned kernel: threads per block and grid waves
+// (waves <= 0: one work item per thread).
+struct Shape {
+  int threads = 256;
+  int waves = 1;
+  int occ = 8;  // resident blocks per SM at this block size
+};
+
 struct ProfileState {
   bool timing = false;
   long long launches[K_COUNT] = {};
@@ -104,6 +121,17 @@ struct hmc_ctx {
   int max_grid = 0;
 
   hmc::ProfileState prof;
+
+  // CUDA graphs of CG iteration chunks (replayed on `stream`; captured on the
+  // private non-blocking `cap_stream`, since the legacy stream cannot capture)
+  hmc::Shape shape[hmc::K_COUNT];
+  bool tuned32 = false, tuned64 = false;
+
+  bool use_graphs = true;
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<hmc::GraphEntry> graphs;
+  long long graph_clock = 0;
 };
 
 namespace hmc {
@@ -111,6 +139,7 @@ namespace hmc {
 constexpr int kThreads = 256;
 constexpr int kMaxGridPerSM = 8;
 constexpr int kOneItemBlocksPerSM = 64;
+constexpr int kMaxThreads = 512;  // largest block of the tuned CG kernels
 constexpr int kMaxRed = 40;  // values reduced at once at most
 constexpr int kTickets = 16;
 
@@ -152,6 +181,20 @@ inline int grid_one(const hmc_ctx* c, long long work) {
   return (int)g;
 }
 
+// Grid of a tuned kernel over `work` items.
+inline int shape_grid(const hmc_ctx* c, int id, long long work) {
+  const Shape& s = c->shape[id];
+  long long g = (work + s.threads - 1) / s.threads;
+  if (s.waves > 0) {
+    const long long cap = (long long)c->nsm * s.occ * s.waves;
+    if (g > cap) g = cap;
+  } else {
+    const long long cap = (long long)c->nsm * kOneItemBlocksPerSM * 256 / s.threads;
+    if (g > cap) g = cap;
+  }
+  return g < 1 ? 1 : (int)g;
+}
+
 // Instrumented launch: counts, and brackets with events when timing is on.
 void prof_begin(hmc_ctx* c, int id, cudaEvent_t* a);
 void prof_end(hmc_ctx* c, int id, cudaEvent_t a);
@@ -160,6 +203,11 @@ void prof_end(hmc_ctx* c, int id, cudaEvent_t a);
 // site times the context's site count.
 template <typename F>
 inline hmc_status launch_b(hmc_ctx* c, int id, double bytes, F&& f) {
+  if (c->capturing) {  // recorded into a graph: counted when the graph is replayed
+    f();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HMC_OK : cuda_fail(c, e, kKernelNames[id]);
+  }
   cudaEvent_t a = nullptr;
   c->prof.bytes[id] += bytes >= 0 ? bytes : kKernelBytesPerSite[id] * (double)c->geo.N;
   prof_begin(c, id, &a);
@@ -174,6 +222,14 @@ template <typename F>
 inline hmc_status launch(hmc_ctx* c, int id, F&& f) {
   return launch_b(c, id, -1.0, f);
 }
+
+// Capture the kernels `body` launches into a graph (on cap_stream) and return
+// the instantiated executable; the context's stream is restored afterwards.
+hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cudaGraphExec_t* out);
+// Cached executable for (kind, key) or NULL.
+GraphEntry* find_graph(hmc_ctx* c, int kind, const void* const key[6]);
+GraphEntry* add_graph(hmc_ctx* c, int kind, const void* const key[6], cudaGraphExec_t exec);
+void destroy_graphs(hmc_ctx* c);
 
 // Build the phase tables of phi (or reuse the loaded field when phi is NULL).
 hmc_status prepare_field(hmc_ctx* c, const double* phi);

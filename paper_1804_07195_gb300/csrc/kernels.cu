@@ -98,11 +98,12 @@ __global__ void __launch_bounds__(kThreads) k_m(Geo g, Phase<R> ph, R dm, const 
 
 // u = M^dagger p; pAp = |u|^2 + sigma |p|^2 = <p, (M M^dagger + sigma) p>; alpha = rr / pAp.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_cg_mdag(Geo g, Phase<R> ph, R dm,
+__global__ void __launch_bounds__(kMaxThreads) k_cg_mdag(Geo g, Phase<R> ph,
                                                       const V2<R>* __restrict__ p,
                                                       V2<R>* __restrict__ u, CGScal* sc,
                                                       double* partials, unsigned* ticket) {
   if (sc->done) return;
+  const R dm = (R)sc->dm;
   const R sigma = (R)sc->sigma;
   double acc[1] = {0.0};
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
@@ -129,12 +130,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_mdag(Geo g, Phase<R> ph, R dm,
 
 // A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_cg_m(Geo g, Phase<R> ph, R dm,
+__global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
                                                    const V2<R>* __restrict__ u,
                                                    const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
                                                    V2<R>* __restrict__ r, CGScal* sc,
                                                    double* partials, unsigned* ticket) {
   if (sc->done) return;
+  const R dm = (R)sc->dm;
   const R sigma = (R)sc->sigma;
   const R alpha = (R)sc->alpha;
   double acc[1] = {0.0};
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_m(Geo g, Phase<R> ph, R dm,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_cg_p(int N, const V2<R>* __restrict__ r,
+__global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __restrict__ r,
                                                    V2<R>* __restrict__ p, const CGScal* sc) {
   if (sc->done) return;
   const R beta = (R)sc->beta;
@@ -193,13 +195,14 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(int N, const V2<R>* __restric
 //   u = M^dagger p_new,  pAp = |u|^2 + sigma |p_new|^2,  alpha = rr / pAp,
 // and p_new is stored at the thread's own sites. beta = 0 on the first
 // iteration (the init kernels set p_old = r, so no NaN can enter).
-__global__ void __launch_bounds__(kThreads) k_cg32_pmdag(Geo g, Phase<float> ph, float dm,
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> ph,
                                                          const float2* __restrict__ r,
                                                          const float2* __restrict__ pold,
                                                          float2* __restrict__ pnew,
                                                          float2* __restrict__ u, CGScal* sc,
                                                          double* partials, unsigned* ticket) {
   if (sc->done) return;
+  const float dm = (float)sc->dm;
   const float sigma = (float)sc->sigma;
   const float beta = (float)sc->beta;
   const int H = g.H;
@@ -243,12 +246,13 @@ __global__ void __launch_bounds__(kThreads) k_cg32_pmdag(Geo g, Phase<float> ph,
 
 // A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2
 // (FP32 vectors; one float partial per thread, reduced in FP64).
-__global__ void __launch_bounds__(kThreads) k_cg32_m(Geo g, Phase<float> ph, float dm,
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
                                                      const float2* __restrict__ u,
                                                      const float2* __restrict__ p,
                                                      float2* __restrict__ x, float2* __restrict__ r,
                                                      CGScal* sc, double* partials, unsigned* ticket) {
   if (sc->done) return;
+  const float dm = (float)sc->dm;
   const float sigma = (float)sc->sigma;
   const float alpha = (float)sc->alpha;
   float loc = 0.f;
@@ -294,8 +298,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
                                                     const V2<R>* __restrict__ b, R sigma,
                                                     V2<R>* __restrict__ r, V2<R>* __restrict__ p,
                                                     CGScal* init, double tol2, int maxit,
-                                                    double dsigma, double* out2, double* partials,
-                                                    unsigned* ticket) {
+                                                    double dsigma, double ddm, double* out2,
+                                                    double* partials, unsigned* ticket) {
   double acc[2] = {0.0, 0.0};
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
     Nbr nb = neighbours(g, q);
@@ -325,6 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
       init->bb = tot[1];
       init->thresh = tol2 * tot[1];
       init->sigma = dsigma;
+      init->dm = ddm;
       init->iter = 0;
       init->maxit = maxit;
       init->alpha = init->beta = init->pAp = 0.0;
@@ -338,8 +343,8 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restrict__ b,
                                                     V2<R>* __restrict__ x, V2<R>* __restrict__ r,
                                                     V2<R>* __restrict__ p, CGScal* sc, double tol2,
-                                                    int maxit, double sigma, double* partials,
-                                                    unsigned* ticket) {
+                                                    int maxit, double sigma, double ddm,
+                                                    double* partials, unsigned* ticket) {
   double acc[1] = {0.0};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     Cx<R> bk = ld<R>(b, k);
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restri
     sc->bb = tot[0];
     sc->thresh = tol2 * tot[0];
     sc->sigma = sigma;
+    sc->dm = ddm;
     sc->iter = 0;
     sc->maxit = maxit;
     sc->alpha = sc->beta = sc->pAp = 0.0;
@@ -554,7 +560,9 @@ __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __res
 
 // ---------------------------------------------------------------------------
 // Launchers
-#define GRID(work) grid_one(c, (work)), kThreads, 0, c->stream
+#define GRID(work) grid_for(c, (work)), kThreads, 0, c->stream
+// tuned launch shape of a CG kernel
+#define SHAPE(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, 0, c->stream
 
 hmc_status k_phase_launch(hmc_ctx* c, const double* phi) {
   const int N = c->geo.N;
@@ -575,38 +583,40 @@ hmc_status m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>*
                 [&] { k_m<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, y, sigma, out); });
 }
 template <typename R>
-hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* u, CGScal* sc,
+hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,
                           unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, [&] {
-    k_cg_mdag<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, p, u, sc, c->partials, ticket);
+    k_cg_mdag<R><<<SHAPE(sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, g.H)>>>(g, phase_of<R>(c), p, u, sc,
+                                                                            c->partials, ticket);
   });
 }
 template <typename R>
-hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* p, V2<R>* x,
+hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, const V2<R>* u, const V2<R>* p, V2<R>* x,
                        V2<R>* r, CGScal* sc, unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, [&] {
-    k_cg_m<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, p, x, r, sc, c->partials, ticket);
+    k_cg_m<R><<<SHAPE(sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, g.H)>>>(g, phase_of<R>(c), u, p, x, r, sc,
+                                                                      c->partials, ticket);
   });
 }
 template <typename R>
 hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc) {
   return launch(c, sizeof(R) == 8 ? K_CG_P64 : K_CG_P32,
-                [&] { k_cg_p<R><<<GRID(N)>>>(N, r, p, sc); });
+                [&] { k_cg_p<R><<<SHAPE(sizeof(R) == 8 ? K_CG_P64 : K_CG_P32, N)>>>(N, r, p, sc); });
 }
 template <typename R>
 hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
                         const V2<R>* b, double sigma, V2<R>* r, V2<R>* p, CGScal* init,
-                        double tol2, int maxit, double* out2, unsigned* ticket) {
+                        double tol2, int maxit, double* out2, unsigned* ticket, double ddm) {
   return launch(c, sizeof(R) == 8 ? K_RESID64 : K_RESID32, [&] {
     k_resid<R><<<GRID(g.H)>>>(g, phase_of<R>(c), dm, u, x, b, (R)sigma, r, p, init, tol2, maxit,
-                              sigma, out2, c->partials, ticket);
+                              sigma, ddm, out2, c->partials, ticket);
   });
 }
 template <typename R>
 hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V2<R>* p, CGScal* sc,
-                        double tol2, int maxit, double sigma, unsigned* ticket) {
+                        double tol2, int maxit, double sigma, unsigned* ticket, double ddm) {
   return launch(c, K_INIT0, [&] {
-    k_init0<R><<<GRID(N)>>>(N, b, x, r, p, sc, tol2, maxit, sigma, c->partials, ticket);
+    k_init0<R><<<GRID(N)>>>(N, b, x, r, p, sc, tol2, maxit, sigma, ddm, c->partials, ticket);
   });
 }
 
@@ -614,33 +624,51 @@ hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V
   template hmc_status mdag_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, V2<R>*);             \
   template hmc_status m_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*, R,        \
                                   V2<R>*);                                                        \
-  template hmc_status cg_mdag_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, V2<R>*, CGScal*,  \
+  template hmc_status cg_mdag_launch<R>(hmc_ctx*, const Geo&, const V2<R>*, V2<R>*, CGScal*,     \
                                         unsigned*);                                               \
-  template hmc_status cg_m_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*,        \
+  template hmc_status cg_m_launch<R>(hmc_ctx*, const Geo&, const V2<R>*, const V2<R>*,           \
                                      V2<R>*, V2<R>*, CGScal*, unsigned*);                         \
   template hmc_status cg_p_launch<R>(hmc_ctx*, int, const V2<R>*, V2<R>*, const CGScal*);        \
   template hmc_status resid_launch<R>(hmc_ctx*, const Geo&, R, const V2<R>*, const V2<R>*,       \
                                       const V2<R>*, double, V2<R>*, V2<R>*, CGScal*, double, int, \
-                                      double*, unsigned*);                                        \
+                                      double*, unsigned*, double);                                \
   template hmc_status init0_launch<R>(hmc_ctx*, int, const V2<R>*, V2<R>*, V2<R>*, V2<R>*,       \
-                                      CGScal*, double, int, double, unsigned*);
+                                      CGScal*, double, int, double, unsigned*, double);
 INST(float)
 INST(double)
 #undef INST
 
-hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, float dm, const float2* r, const float2* pold,
+hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    k_cg32_pmdag<<<grid_one(c, g.H), kThreads, 0, c->stream>>>(g, phase_of<float>(c), dm, r, pold, pnew,
+    k_cg32_pmdag<<<SHAPE(K_CG_MDAG32, g.H)>>>(g, phase_of<float>(c), r, pold, pnew,
                                                               u, sc, c->partials, ticket);
   });
 }
-hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, float dm, const float2* u, const float2* p, float2* x,
+hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    k_cg32_m<<<grid_one(c, g.H), kThreads, 0, c->stream>>>(g, phase_of<float>(c), dm, u, p, x, r, sc,
+    k_cg32_m<<<SHAPE(K_CG_M32, g.H)>>>(g, phase_of<float>(c), u, p, x, r, sc,
                                                           c->partials, ticket);
   });
+}
+
+int cg_kernel_occupancy(int id, int threads) {
+  int nb = 0;
+  const void* f = nullptr;
+  switch (id) {
+    case K_CG_MDAG64: f = (const void*)k_cg_mdag<double>; break;
+    case K_CG_M64: f = (const void*)k_cg_m<double>; break;
+    case K_CG_P64: f = (const void*)k_cg_p<double>; break;
+    case K_CG_MDAG32: f = (const void*)k_cg32_pmdag; break;
+    case K_CG_M32: f = (const void*)k_cg32_m; break;
+    default: return 1;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
 }
 
 hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out) {

@@ -21,10 +21,10 @@ hmc_status m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>*
 
 // CG building blocks on the state sc (see common.cuh).
 template <typename R>
-hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* p, V2<R>* u, CGScal* sc,
+hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,
                           unsigned* ticket);
 template <typename R>
-hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* p, V2<R>* x,
+hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, const V2<R>* u, const V2<R>* p, V2<R>* x,
                        V2<R>* r, CGScal* sc, unsigned* ticket);
 template <typename R>
 hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc);
@@ -32,23 +32,27 @@ hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal
 // FP32 CG, two kernels per iteration: p_new = r + beta p_old folded into
 // u = M^dagger p_new (with pAp and alpha), then the M kernel with the updates.
 // One cell-time per thread.
-hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, float dm, const float2* r, const float2* pold,
+hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket);
-hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, float dm, const float2* u, const float2* p, float2* x,
+hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket);
 
 // r = b - (M u + sigma x), with |r|^2 and |b|^2 reduced. When init != NULL the
 // last block initialises a CG state (rr, bb, thresh = tol2 * bb, iter 0, done if
-// rr <= thresh) and p = r is written. When out2 != NULL it receives {|r|^2, |b|^2}.
+// rr <= thresh, the operator's sigma and ddm = delta m_s) and p = r is written.
+// When out2 != NULL it receives {|r|^2, |b|^2}.
 template <typename R>
 hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
                         const V2<R>* b, double sigma, V2<R>* r, V2<R>* p, CGScal* init,
-                        double tol2, int maxit, double* out2, unsigned* ticket);
+                        double tol2, int maxit, double* out2, unsigned* ticket, double ddm = 0.0);
 
-// x = 0, r = p = b, |b|^2 reduced into a fresh CG state.
+// x = 0, r = p = b, |b|^2 reduced into a fresh CG state (with sigma, ddm).
 template <typename R>
 hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V2<R>* p, CGScal* sc,
-                        double tol2, int maxit, double sigma, unsigned* ticket);
+                        double tol2, int maxit, double sigma, unsigned* ticket, double ddm);
+
+// Resident blocks per SM of a CG kernel at `threads` threads per block.
+int cg_kernel_occupancy(int id, int threads);
 
 // Precision conversions.
 hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out);

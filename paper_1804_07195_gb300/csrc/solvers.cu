@@ -42,10 +42,85 @@ static hmc_status vec_slots(hmc_ctx* c, V2<R>** r, V2<R>** p, V2<R>** u) {
   return HMC_OK;
 }
 
+// Launch-shape autotuner of the CG kernels of one precision: every candidate
+// (threads per block x grid waves, the same for all kernels of the iteration)
+// runs a few timed iterations on scratch vectors with this solve's right-hand
+// side; the fastest is kept for the context. Runs once per context and
+// precision. Results of later solves are reproducible for the chosen shape
+// (the shape fixes the reduction order).
+template <typename R>
+static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
+  bool& done = sizeof(R) == 4 ? c->tuned32 : c->tuned64;
+  if (done) return HMC_OK;
+  done = true;
+  const Geo& g = c->geo;
+  const size_t bytes = sizeof(V2<R>) * (size_t)g.N;
+  V2<R> *r, *p, *u, *x, *q = nullptr;
+  HMC_TRY(vec_slots<R>(c, &r, &p, &u));
+  HMC_TRY(ws_get(c, sizeof(R) == 4 ? WS_CG_X32 : WS_CG_X64, bytes, (void**)&x));
+  if (sizeof(R) == 4) HMC_TRY(ws_get(c, WS_CG_Q32, bytes, (void**)&q));
+  CGScal* sc = c->sc + 2;
+  unsigned* tk = c->tickets;
+  const int ids32[2] = {K_CG_MDAG32, K_CG_M32};
+  const int ids64[3] = {K_CG_MDAG64, K_CG_M64, K_CG_P64};
+  const int* ids = sizeof(R) == 4 ? ids32 : ids64;
+  const int nk = sizeof(R) == 4 ? 2 : 3;
+  auto iter = [&](int n) -> hmc_status {
+    for (int i = 0; i < n; ++i) {
+      if constexpr (sizeof(R) == 4) {
+        float2* po = (i & 1) ? (float2*)q : (float2*)p;
+        float2* pn = (i & 1) ? (float2*)p : (float2*)q;
+        HMC_TRY(cg32_pmdag_launch(c, g, (const float2*)r, po, pn, (float2*)u, sc, tk));
+        HMC_TRY(cg32_m_launch(c, g, (const float2*)u, pn, (float2*)x, (float2*)r, sc, tk));
+      } else {
+        HMC_TRY(cg_mdag_launch<R>(c, g, p, u, sc, tk));
+        HMC_TRY(cg_m_launch<R>(c, g, u, p, x, r, sc, tk));
+        HMC_TRY(cg_p_launch<R>(c, g.N, r, p, sc));
+      }
+    }
+    return HMC_OK;
+  };
+  cudaEvent_t e0, e1;
+  HMC_CUDA(c, cudaEventCreate(&e0));
+  HMC_CUDA(c, cudaEventCreate(&e1));
+  const int threads[3] = {128, 256, 512};
+  const int waves[4] = {1, 2, 4, 0};
+  float best = 1e30f;
+  Shape keep[3];
+  for (int ti = 0; ti < 3; ++ti) {
+    for (int wi = 0; wi < 4; ++wi) {
+      for (int k = 0; k < nk; ++k) {
+        Shape& sh = c->shape[ids[k]];
+        sh.threads = threads[ti];
+        sh.waves = waves[wi];
+        sh.occ = cg_kernel_occupancy(ids[k], threads[ti]);
+      }
+      // tolerance 0: no candidate stops early
+      HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, 0.0, 1 << 30, sigma, tk, c->delta * ms));
+      HMC_TRY(iter(2));
+      HMC_CUDA(c, cudaEventRecord(e0, c->stream));
+      HMC_TRY(iter(4));
+      HMC_CUDA(c, cudaEventRecord(e1, c->stream));
+      HMC_CUDA(c, cudaEventSynchronize(e1));
+      float ms_ = 0.f;
+      cudaEventElapsedTime(&ms_, e0, e1);
+      if (ms_ < best) {
+        best = ms_;
+        for (int k = 0; k < nk; ++k) keep[k] = c->shape[ids[k]];
+      }
+    }
+  }
+  for (int k = 0; k < nk; ++k) c->shape[ids[k]] = keep[k];
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return HMC_OK;
+}
+
 template <typename R>
 hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x, bool x_zero,
                    double tol, int maxit, int sc_slot, bool want_true_res, SolveStats* st) {
   const Geo& g = c->geo;
+  if (!c->capturing) HMC_TRY(tune_cg<R>(c, ms, sigma, b));
   const R dm = (R)(c->delta * ms);
   V2<R> *r, *p, *u;
   HMC_TRY(vec_slots<R>(c, &r, &p, &u));
@@ -53,47 +128,81 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   CGScal* sch = c->sc_host + sc_slot;
   unsigned* tk = c->tickets;
   const double tol2 = tol * tol;
+  const double ddm = c->delta * ms;
   if (x_zero) {
-    HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, tol2, maxit, sigma, tk));
+    HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, tol2, maxit, sigma, tk, ddm));
   } else {
     HMC_TRY(mdag_launch<R>(c, g, dm, x, u));
-    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, p, sc, tol2, maxit, nullptr, tk));
+    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, p, sc, tol2, maxit, nullptr, tk, ddm));
     if (sizeof(R) == 8) st->applies64++; else st->applies32++;
   }
   // FP32: two kernels per iteration with a second direction buffer q
-  // (p and q alternate as p_old / p_new); the chunk length stays even so an
-  // iteration count that ends a chunk leaves the newest direction in p.
+  // (p and q alternate as p_old / p_new); every chunk has an even length, so
+  // the newest direction is in p whenever a chunk ends.
   V2<R>* q = nullptr;
   if (sizeof(R) == 4)
     HMC_TRY(ws_get(c, WS_CG_Q32, sizeof(V2<R>) * (size_t)g.N, (void**)&q));
-  int chunk = 4;
-  int launched = 0;
-  for (;;) {
-    for (int i = 0; i < chunk; ++i) {
+  auto iterate = [&](int n) -> hmc_status {
+    for (int i = 0; i < n; ++i) {
       if constexpr (sizeof(R) == 4) {
         float2* pold = (i & 1) ? (float2*)q : (float2*)p;
         float2* pnew = (i & 1) ? (float2*)p : (float2*)q;
-        HMC_TRY(cg32_pmdag_launch(c, g, (float)dm, (const float2*)r, pold, pnew, (float2*)u, sc, tk));
-        HMC_TRY(cg32_m_launch(c, g, (float)dm, (const float2*)u, pnew, (float2*)x, (float2*)r, sc, tk));
+        HMC_TRY(cg32_pmdag_launch(c, g, (const float2*)r, pold, pnew, (float2*)u, sc, tk));
+        HMC_TRY(cg32_m_launch(c, g, (const float2*)u, pnew, (float2*)x, (float2*)r, sc, tk));
       } else {
-        HMC_TRY(cg_mdag_launch<R>(c, g, dm, p, u, sc, tk));
-        HMC_TRY(cg_m_launch<R>(c, g, dm, u, p, x, r, sc, tk));
+        HMC_TRY(cg_mdag_launch<R>(c, g, p, u, sc, tk));
+        HMC_TRY(cg_m_launch<R>(c, g, u, p, x, r, sc, tk));
         HMC_TRY(cg_p_launch<R>(c, g.N, r, p, sc));
       }
     }
-    launched += chunk;
+    return HMC_OK;
+  };
+  // Iterations run in chunks of kChunk, replayed from a captured CUDA graph
+  // (one per buffer set) unless per-kernel timing is on; the host reads the
+  // state after 1, 1, 2, 4, 4, ... chunks.
+  constexpr int kChunk = 8;
+  GraphEntry* ge = nullptr;
+  if (c->use_graphs && !c->prof.timing) {
+    const void* key[6] = {sc, r, p, q, u, x};
+    const int kind = sizeof(R) == 4 ? 32 : 64;
+    ge = find_graph(c, kind, key);
+    if (!ge) {
+      cudaGraphExec_t exec;
+      HMC_TRY(capture_graph(c, [&] { return iterate(kChunk); }, &exec));
+      ge = add_graph(c, kind, key, exec);
+    }
+  }
+  const int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64,
+                      K_CG_P64};
+  const double kbytes[3] = {sizeof(R) == 4 ? 36.0 : 48.0, sizeof(R) == 4 ? 52.0 : 112.0, 48.0};
+  const int nk = sizeof(R) == 4 ? 2 : 3;
+  int per_check = 1, checks = 0;
+  long long launched = 0;
+  for (;;) {
+    for (int i = 0; i < per_check; ++i) {
+      if (ge) {
+        HMC_CUDA(c, cudaGraphLaunch(ge->exec, c->stream));
+        for (int k = 0; k < nk; ++k) {
+          c->prof.launches[kid[k]] += kChunk;
+          c->prof.bytes[kid[k]] += kChunk * kbytes[k] * g.N;
+        }
+      } else {
+        HMC_TRY(iterate(kChunk));
+      }
+    }
+    launched += (long long)per_check * kChunk;
     HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
     HMC_CUDA(c, cudaStreamSynchronize(c->stream));
     if (sch->done != CG_RUNNING) break;
-    if (launched > maxit + 64) break;  // cannot happen: the device stops at maxit
-    if (chunk < 32) chunk *= 2;
+    if (launched > (long long)maxit + 2 * kChunk) break;  // cannot happen: the device stops at maxit
+    if (++checks >= 2 && per_check < 4) per_check *= 2;
   }
   st->iters += sch->iter;
   if (sizeof(R) == 8) st->applies64 += sch->iter; else st->applies32 += sch->iter;
   st->cg_done = sch->done;
   if (want_true_res) {
     HMC_TRY(mdag_launch<R>(c, g, dm, x, u));
-    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, nullptr, nullptr, 0.0, 0, c->dscal, tk));
+    HMC_TRY(resid_launch<R>(c, g, dm, u, x, b, sigma, r, nullptr, nullptr, 0.0, 0, c->dscal, tk, ddm));
     HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host, c->dscal, 2 * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
     HMC_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -209,6 +209,16 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsig
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may be scheduled before the previous
+// kernel in the stream has finished; pdl_wait() blocks until that kernel has
+// completed and its memory is visible, and pdl_trigger() lets the next kernel
+// start launching once every block of this one has passed it. Both are no-ops
+// for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// ---------------------------------------------------------------------------
 // Device-side scalar state of one CG solve (shared by the FP64 and FP32 paths).
 struct CGScal {
   double rr;     // |r|^2 of the current residual

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_mdag(Geo g, Phase<R> ph,
                                                       const V2<R>* __restrict__ p,
                                                       V2<R>* __restrict__ u, CGScal* sc,
                                                       double* partials, unsigned* ticket) {
+  pdl_wait();
   if (sc->done) return;
   const R dm = (R)sc->dm;
   const R sigma = (R)sc->sigma;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_mdag(Geo g, Phase<R> ph,
     if (sigma != (R)0) loc += sigma * (norm2(ld<R>(p, q)) + norm2(ld<R>(p, g.H + q)));
     acc[0] += (double)loc;
   }
+  pdl_trigger();
   double tot[1];
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
     double pAp = tot[0];
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
                                                    const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
                                                    V2<R>* __restrict__ r, CGScal* sc,
                                                    double* partials, unsigned* ticket) {
+  pdl_wait();
   if (sc->done) return;
   const R dm = (R)sc->dm;
   const R sigma = (R)sc->sigma;
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
     }
     acc[0] += (double)loc;
   }
+  pdl_trigger();
   double tot[1];
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
     double rr = tot[0];
@@ -179,7 +183,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
 template <typename R>
 __global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __restrict__ r,
                                                    V2<R>* __restrict__ p, const CGScal* sc) {
+  pdl_wait();
   if (sc->done) return;
+  pdl_trigger();
   const R beta = (R)sc->beta;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     Cx<R> rk = ld<R>(r, k), pk = ld<R>(p, k);
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
                                                          float2* __restrict__ pnew,
                                                          float2* __restrict__ u, CGScal* sc,
                                                          double* partials, unsigned* ticket) {
+  pdl_wait();
   if (sc->done) return;
   const float dm = (float)sc->dm;
   const float sigma = (float)sc->sigma;
@@ -230,6 +237,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
     loc += norm2(oa) + norm2(ob);
     if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
   }
+  pdl_trigger();
   double acc[1] = {(double)loc};
   double tot[1];
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
@@ -251,6 +259,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
                                                      const float2* __restrict__ p,
                                                      float2* __restrict__ x, float2* __restrict__ r,
                                                      CGScal* sc, double* partials, unsigned* ticket) {
+  pdl_wait();
   if (sc->done) return;
   const float dm = (float)sc->dm;
   const float sigma = (float)sc->sigma;
@@ -275,6 +284,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
       loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
     }
   }
+  pdl_trigger();
   double acc[1] = {(double)loc};
   double tot[1];
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
@@ -561,6 +571,29 @@ __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __res
 // ---------------------------------------------------------------------------
 // Launchers
 #define GRID(work) grid_for(c, (work)), kThreads, 0, c->stream
+// Launch with the programmatic-serialization attribute (see pdl_wait).
+// Only on an explicit non-blocking stream (the capture stream): on the legacy
+// default stream the kernel is launched the ordinary way.
+template <typename... KA, typename... A>
+static void launch_pdl(void (*k)(KA...), int grid, int threads, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  unsigned flags = 0;
+  const bool explicit_stream = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread &&
+                               cudaStreamGetFlags(s, &flags) == cudaSuccess &&
+                               (flags & cudaStreamNonBlocking);
+  cfg.attrs = explicit_stream ? attr : nullptr;
+  cfg.numAttrs = explicit_stream ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, k, ((KA)args)...);  // errors surface through cudaGetLastError
+}
+#define PDL(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, c->stream
+
 // tuned launch shape of a CG kernel
 #define SHAPE(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, 0, c->stream
 
@@ -586,22 +619,22 @@ template <typename R>
 hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,
                           unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, [&] {
-    k_cg_mdag<R><<<SHAPE(sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, g.H)>>>(g, phase_of<R>(c), p, u, sc,
-                                                                            c->partials, ticket);
+    launch_pdl(k_cg_mdag<R>, PDL(sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, g.H), g, phase_of<R>(c), p,
+               u, sc, c->partials, ticket);
   });
 }
 template <typename R>
 hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, const V2<R>* u, const V2<R>* p, V2<R>* x,
                        V2<R>* r, CGScal* sc, unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, [&] {
-    k_cg_m<R><<<SHAPE(sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, g.H)>>>(g, phase_of<R>(c), u, p, x, r, sc,
-                                                                      c->partials, ticket);
+    launch_pdl(k_cg_m<R>, PDL(sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, g.H), g, phase_of<R>(c), u, p, x, r,
+               sc, c->partials, ticket);
   });
 }
 template <typename R>
 hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc) {
   return launch(c, sizeof(R) == 8 ? K_CG_P64 : K_CG_P32,
-                [&] { k_cg_p<R><<<SHAPE(sizeof(R) == 8 ? K_CG_P64 : K_CG_P32, N)>>>(N, r, p, sc); });
+                [&] { launch_pdl(k_cg_p<R>, PDL(sizeof(R) == 8 ? K_CG_P64 : K_CG_P32, N), N, r, p, sc); });
 }
 template <typename R>
 hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
@@ -641,15 +674,14 @@ INST(double)
 hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    k_cg32_pmdag<<<SHAPE(K_CG_MDAG32, g.H)>>>(g, phase_of<float>(c), r, pold, pnew,
-                                                              u, sc, c->partials, ticket);
+    launch_pdl(k_cg32_pmdag, PDL(K_CG_MDAG32, g.H), g, phase_of<float>(c), r, pold, pnew, u, sc,
+               c->partials, ticket);
   });
 }
 hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    k_cg32_m<<<SHAPE(K_CG_M32, g.H)>>>(g, phase_of<float>(c), u, p, x, r, sc,
-                                                          c->partials, ticket);
+    launch_pdl(k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc, c->partials, ticket);
   });
 }
 

@@ -93,6 +93,7 @@ hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cu
   cudaStream_t saved = c->stream;
   c->stream = c->cap_stream;
   c->capturing = true;
+  c->pdl_armed = false;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   hmc_status st = e == cudaSuccess ? body() : cuda_fail(c, e, "cudaStreamBeginCapture");
   cudaGraph_t graph = nullptr;
@@ -101,12 +102,14 @@ hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cu
     if (e2 != cudaSuccess && st == HMC_OK) st = cuda_fail(c, e2, "cudaStreamEndCapture");
   }
   c->capturing = false;
+  c->pdl_armed = false;
   c->stream = saved;
   if (st == HMC_OK && graph) {
     e = cudaGraphInstantiate(out, graph, 0);
     if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGraphInstantiate");
   }
   if (graph) cudaGraphDestroy(graph);
+  if (st != HMC_OK) cudaGetLastError();  // a failed capture leaves no error behind
   return st;
 }
 

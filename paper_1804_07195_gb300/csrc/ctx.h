@@ -129,6 +129,7 @@ struct hmc_ctx {
 
   bool use_graphs = true;
   bool capturing = false;
+  bool pdl_armed = false;  // a kernel precedes the next launch in the capture
   cudaStream_t cap_stream = nullptr;
   std::vector<hmc::GraphEntry> graphs;
   long long graph_clock = 0;

@@ -572,10 +572,11 @@ __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __res
 // Launchers
 #define GRID(work) grid_for(c, (work)), kThreads, 0, c->stream
 // Launch with the programmatic-serialization attribute (see pdl_wait).
-// Only on an explicit non-blocking stream (the capture stream): on the legacy
-// default stream the kernel is launched the ordinary way.
+// Programmatic launches are used only between consecutive kernels of a
+// captured iteration chunk: the first kernel of a capture (no kernel before it
+// in the graph) and every launch outside a capture are ordinary launches.
 template <typename... KA, typename... A>
-static void launch_pdl(void (*k)(KA...), int grid, int threads, cudaStream_t s, A... args) {
+static void launch_pdl(hmc_ctx* c, void (*k)(KA...), int grid, int threads, cudaStream_t s, A... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
@@ -584,13 +585,11 @@ static void launch_pdl(void (*k)(KA...), int grid, int threads, cudaStream_t s, 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
-  unsigned flags = 0;
-  const bool explicit_stream = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread &&
-                               cudaStreamGetFlags(s, &flags) == cudaSuccess &&
-                               (flags & cudaStreamNonBlocking);
-  cfg.attrs = explicit_stream ? attr : nullptr;
-  cfg.numAttrs = explicit_stream ? 1 : 0;
+  const bool pdl = c->capturing && c->pdl_armed;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
   (void)cudaLaunchKernelEx(&cfg, k, ((KA)args)...);  // errors surface through cudaGetLastError
+  if (c->capturing) c->pdl_armed = true;
 }
 #define PDL(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, c->stream
 
@@ -619,7 +618,7 @@ template <typename R>
 hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,
                           unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, [&] {
-    launch_pdl(k_cg_mdag<R>, PDL(sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, g.H), g, phase_of<R>(c), p,
+    launch_pdl(c, k_cg_mdag<R>, PDL(sizeof(R) == 8 ? K_CG_MDAG64 : K_CG_MDAG32, g.H), g, phase_of<R>(c), p,
                u, sc, c->partials, ticket);
   });
 }
@@ -627,14 +626,14 @@ template <typename R>
 hmc_status cg_m_launch(hmc_ctx* c, const Geo& g, const V2<R>* u, const V2<R>* p, V2<R>* x,
                        V2<R>* r, CGScal* sc, unsigned* ticket) {
   return launch(c, sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, [&] {
-    launch_pdl(k_cg_m<R>, PDL(sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, g.H), g, phase_of<R>(c), u, p, x, r,
+    launch_pdl(c, k_cg_m<R>, PDL(sizeof(R) == 8 ? K_CG_M64 : K_CG_M32, g.H), g, phase_of<R>(c), u, p, x, r,
                sc, c->partials, ticket);
   });
 }
 template <typename R>
 hmc_status cg_p_launch(hmc_ctx* c, int N, const V2<R>* r, V2<R>* p, const CGScal* sc) {
   return launch(c, sizeof(R) == 8 ? K_CG_P64 : K_CG_P32,
-                [&] { launch_pdl(k_cg_p<R>, PDL(sizeof(R) == 8 ? K_CG_P64 : K_CG_P32, N), N, r, p, sc); });
+                [&] { launch_pdl(c, k_cg_p<R>, PDL(sizeof(R) == 8 ? K_CG_P64 : K_CG_P32, N), N, r, p, sc); });
 }
 template <typename R>
 hmc_status resid_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* x,
@@ -674,14 +673,14 @@ INST(double)
 hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    launch_pdl(k_cg32_pmdag, PDL(K_CG_MDAG32, g.H), g, phase_of<float>(c), r, pold, pnew, u, sc,
+    launch_pdl(c, k_cg32_pmdag, PDL(K_CG_MDAG32, g.H), g, phase_of<float>(c), r, pold, pnew, u, sc,
                c->partials, ticket);
   });
 }
 hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket) {
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    launch_pdl(k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc, c->partials, ticket);
+    launch_pdl(c, k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc, c->partials, ticket);
   });
 }
 

@@ -168,8 +168,12 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
     ge = find_graph(c, kind, key);
     if (!ge) {
       cudaGraphExec_t exec;
-      HMC_TRY(capture_graph(c, [&] { return iterate(kChunk); }, &exec));
-      ge = add_graph(c, kind, key, exec);
+      if (capture_graph(c, [&] { return iterate(kChunk); }, &exec) == HMC_OK) {
+        ge = add_graph(c, kind, key, exec);
+      } else {
+        c->use_graphs = false;  // launch the same kernels one by one from now on
+        c->err.clear();
+      }
     }
   }
   const int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64,

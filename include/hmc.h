@@ -272,6 +272,37 @@ hmc_status hmc_profile(hmc_ctx* ctx, int timing_on, int reset);
 /* Copy up to max entries of the per-kernel statistics; *count receives the number written. */
 hmc_status hmc_profile_read(hmc_ctx* ctx, hmc_kernel_stat* out, int max, int* count);
 
+/* ---- one call that allocates nothing ----------------------------------------- */
+
+/* The paper has no counterpart to this entry point.
+ *
+ * out = (M[phi; m_s] M[phi; m_s]^dagger + sigma) in for complex128 vectors, the
+ * same operator as hmc_apply_MMdag, for callers that cannot allocate device
+ * memory: code that runs while its stream is being captured into a CUDA graph
+ * (cudaMalloc is not permitted there), frameworks whose memory pool already
+ * owns the device (a raw cudaMalloc beside it fails or fragments it), and
+ * latency-bound loops that cannot afford an allocation and the device
+ * synchronisation it implies. It needs no context and allocates nothing: the
+ * M^dagger intermediate lives in a static device array of
+ * HMC_NOALLOC_MAX_SITES complex128 entries (16 MiB), which every GPU that
+ * loads this library holds until the process exits, and the phases e^{i phi}
+ * are computed from phi inline.
+ *
+ * lat: the lattice (as for hmc_create); phi: N doubles; in, out: N complex128,
+ * device memory of the current device, not overlapping; sigma >= 0;
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Returns HMC_ERR_NOMEM for a lattice with more than HMC_NOALLOC_MAX_SITES
+ * sites (N = 2 n m nt), HMC_ERR_INVALID for bad arguments, HMC_ERR_CUDA when a
+ * CUDA call fails. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress): make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (on different streams or from
+ * different host threads) race on it and corrupt each other's results, so
+ * serialise them. Asynchronous. */
+#define HMC_NOALLOC_MAX_SITES (1 << 20)
+hmc_status hmc_apply_MMdag_noalloc(const hmc_lattice* lat, const double* phi, double ms, double sigma,
+                                   const void* in, void* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

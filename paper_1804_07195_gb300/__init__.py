@@ -294,4 +294,22 @@ class Context:
                 for i in range(cnt.value)}
 
 
+def apply_MMdag_noalloc(lattice: Lattice, phi, ms, x, sigma=0.0, out=None, stream=None):
+    """out = (M M^dagger + sigma) x (complex128) through hmc_apply_MMdag_noalloc:
+    no context and no device allocation inside the library (the intermediate
+    lives in its static scratch array of HMC_NOALLOC_MAX_SITES entries)."""
+    import torch
+    lib = library()
+    n = lattice.nsites
+    out = torch.empty_like(x) if out is None else out
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib.hmc_apply_MMdag_noalloc(C.byref(lattice.c()), _ptr(phi, torch.float64, n, "phi"), ms, sigma,
+                                     _ptr(x, torch.complex128, n, "x"), _ptr(out, torch.complex128, n, "out"),
+                                     C.c_void_p(stream.cuda_stream))
+    if st != _abi.HMC_OK:
+        raise HMCError(st, "hmc_apply_MMdag_noalloc failed")
+    return out
+
+
 from .autograd import PseudofermionAction  # noqa: E402

@@ -67,6 +67,7 @@ class hmc_kernel_stat(C.Structure):
 
 
 HMC_NKERNELS = 32
+HMC_NOALLOC_MAX_SITES = 1 << 20
 
 P = C.c_void_p
 D = C.c_double
@@ -99,6 +100,7 @@ PROTOTYPES = {
                               C.POINTER(hmc_solver_opts), C.POINTER(hmc_solver_opts),
                               C.POINTER(D), C.POINTER(D), C.POINTER(hmc_solve_info)]),
     "hmc_profile": (S, [P, I, I]),
+    "hmc_apply_MMdag_noalloc": (S, [C.POINTER(hmc_lattice), P, D, D, P, P, P]),
     "hmc_profile_read": (S, [P, C.POINTER(hmc_kernel_stat), I, C.POINTER(I)]),
 }
 

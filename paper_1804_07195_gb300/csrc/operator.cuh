@@ -65,9 +65,10 @@ struct PairOut {
   Cx<R> a, b;
 };
 
-// M^dagger applied at the cell-time of nb, reading p (precision R).
-template <typename R>
-__device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const Phase<R>& ph, R dm,
+// M^dagger applied at the cell-time of nb, reading p (precision R); PH is any
+// functor returning e^{i phi_k}.
+template <typename R, typename PH = Phase<R>>
+__device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const PH& ph, R dm,
                                                 const typename Vec2<R>::type* __restrict__ p,
                                                 const Nbr& nb) {
   const int H = g.H;
@@ -87,8 +88,8 @@ __device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const Phase<R>& ph
 }
 
 // M applied at the cell-time of nb, reading u (precision R).
-template <typename R>
-__device__ __forceinline__ PairOut<R> m_pair(const Geo& g, const Phase<R>& ph, R dm,
+template <typename R, typename PH = Phase<R>>
+__device__ __forceinline__ PairOut<R> m_pair(const Geo& g, const PH& ph, R dm,
                                              const typename Vec2<R>::type* __restrict__ u,
                                              const Nbr& nb) {
   const int H = g.H;

@@ -199,7 +199,7 @@ def main():
     nsteps_total = args.warmup + args.steps + 1 + args.e2e_steps
 
     def step_inputs(k):
-        g = W.rng([W.SEEDS["C5"], rank, k])
+        g = W.rng(replica_seed(W.SEEDS["C5"], rank, k))
         pi = W.draw_pi(g, N)
         rho = [W.draw_complex(g, N) for _ in range(len(masses) + 1)]
         return pi, rho
@@ -259,14 +259,7 @@ def main():
     gpu_launches = int(sum(v["launches"] for v in launches.values()))
 
     # max over ranks of the time, sum of the work
-    sites_applied = float(N) * applies
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        s = torch.tensor([sites_applied], device=dev, dtype=torch.float64)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        sites_applied = float(s.item())
+    total_ms, sites_applied = aggregate_over_ranks(total_ms, float(N) * applies, dist, dev)
     value = sites_applied / (total_ms * 1e-3) / 1e9
 
     # one extra step with CUDA events around every library launch: per-kernel
@@ -325,6 +318,10 @@ def main():
     solve["speedup_mixed_vs_fp64"] = solve["fp64_cg"]["ms"] / solve["mixed_fgmres"]["ms"]
     solve["workload"] = "102x102x64 lattice, m_s=0, phi of the step, b = rho_0, true residual 1e-10"
 
+    # the batched workload: 48 uneven lattices x 3 masses = 144 systems at 1e-10,
+    # batched mixed vs batched FP64 vs FP64 CG one system at a time
+    solve["c4_batched"] = batched_solve_times(hmc, W, torch, stream, flush)
+
     # end to end through the public API with host buffers
     e2e_val = None
     h2d = d2h = 0
@@ -375,6 +372,80 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batched_solve_times(hmc, W, torch, stream, flush):
+    systems, ctxs = [], {}
+    for w in W.c4_instances():
+        p = w.lat
+        lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+        key = (p.n, p.m, p.nt)
+        if key not in ctxs:
+            ctxs[key] = hmc.Context(lat)
+        phi = torch.tensor(w.phi, device="cuda")
+        for ms, b in zip(w.masses, w.rho):
+            systems.append({"lattice": lat, "phi": phi, "ms": ms, "b": torch.tensor(b, device="cuda"),
+                            "x": torch.zeros(p.nsites, dtype=torch.complex128, device="cuda"),
+                            "tol": 1e-10, "key": key})
+    any_ctx = next(iter(ctxs.values()))
+
+    def timed(fn):
+        fn()  # warm (autotuning, graph capture)
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z), r
+
+    def seq(method):
+        worst = 0.0
+        for sy in systems:
+            c = ctxs[sy["key"]]
+            if method == "cg":
+                _, info = c.solve_cg(sy["phi"], sy["ms"], sy["b"], tol=1e-10)
+            else:
+                _, info = c.solve_fgmres(sy["phi"], sy["ms"], sy["b"], tol=1e-10)
+            worst = max(worst, info["true_rel_res"])
+        return worst
+
+    out = {"systems": len(systems), "sites": int(sum(sy["lattice"].nsites for sy in systems))}
+    ms, infos = timed(lambda: any_ctx.solve_batched(systems, mixed=True))
+    out["batched_mixed_ms"] = ms
+    out["batched_mixed_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)
+    ms, infos = timed(lambda: any_ctx.solve_batched(systems, mixed=False))
+    out["batched_fp64_ms"] = ms
+    out["batched_fp64_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)
+    ms, worst = timed(lambda: seq("cg"))
+    out["sequential_fp64_cg_ms"] = ms
+    out["sequential_fp64_cg_max_true_rel_res"] = worst
+    ms, worst = timed(lambda: seq("fgmres"))
+    out["sequential_mixed_fgmres_ms"] = ms
+    out["speedup_batched_mixed_vs_sequential_fp64"] = out["sequential_fp64_cg_ms"] / out["batched_mixed_ms"]
+    for c in ctxs.values():
+        c.close()
+    return out
+
+
+def replica_seed(base, rank, step):
+    """Seed of the inputs of step `step` on rank `rank`: every rank runs its own
+    independent trajectories (replicas), so the streams must differ by rank."""
+    return [int(base), int(rank), int(step)]
+
+
+def aggregate_over_ranks(ms, work, dist, device=None):
+    """Whole-job timing of replicas: the slowest rank's time and the summed work
+    (the only cross-rank communication of the benchmark; none on the data path)."""
+    if dist is None:
+        return float(ms), float(work)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
 
 
 def kernel_case(case):

@@ -229,8 +229,12 @@ hmc_status hmc_force(hmc_ctx* ctx, const double* phi, int nmass, const double* m
                      const void* const* chi, int term, int flags, const hmc_solver_opts* opts,
                      double* dSdphi, hmc_solve_info* info);
 
-/* The action S (same terms and flags as hmc_force) as one host double, with
- * S_i = src_i^dagger eta_i. Synchronous. */
+/* The action S (same terms and flags as hmc_force) as one host double. Each
+ * S_i = src_i^dagger (M_{i-1} M_{i-1}^dagger)^{-1} src_i is evaluated in the
+ * stationary form 2 Re(src_i^dagger eta_i) - |M_{i-1}^dagger eta_i|^2, equal to
+ * the definition for the exact eta_i and with an error second order in the
+ * solve residual (flexible GMRES is not a Galerkin method, so src^dagger eta
+ * alone would carry a first-order error). Synchronous. */
 hmc_status hmc_action(hmc_ctx* ctx, const double* phi, int nmass, const double* masses,
                       const void* const* chi, int term, int flags, const hmc_solver_opts* opts,
                       double* S_out, hmc_solve_info* info);

@@ -235,6 +235,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   c->ws_bytes[WS_PHI32] = N * sizeof(float);
   const size_t npart = (size_t)kMaxRed * std::max(c->max_grid, c->nsm * kOneItemBlocksPerSM);
   if ((e = cudaMalloc(&c->partials, sizeof(double) * npart)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->partA, sizeof(double) * c->nsm * 2 * kOneItemBlocksPerSM)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->partB, sizeof(double) * c->nsm * 2 * kOneItemBlocksPerSM)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->tickets, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
@@ -244,8 +246,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   if ((e = cudaMalloc(&c->partials, sizeof(double) * kMaxRed * c->nsm * 2 * kOneItemBlocksPerSM)) != cudaSuccess)
     return bail(e);
   if ((e = cudaMallocHost(&c->sc_host, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
-  if ((e = cudaMalloc(&c->dscal, sizeof(double) * 64)) != cudaSuccess) return bail(e);
-  if ((e = cudaMallocHost(&c->dscal_host, sizeof(double) * 64)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->dscal, sizeof(double) * 128)) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->dscal_host, sizeof(double) * 128)) != cudaSuccess) return bail(e);
   *out = c;
   return HMC_OK;
 }
@@ -258,6 +260,8 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   for (int i = 0; i < WS_COUNT; ++i)
     if (c->ws[i]) cudaFree(c->ws[i]);
   if (c->partials) cudaFree(c->partials);
+  if (c->partA) cudaFree(c->partA);
+  if (c->partB) cudaFree(c->partB);
   if (c->tickets) cudaFree(c->tickets);
   if (c->sc) cudaFree(c->sc);
   if (c->sc_host) cudaFreeHost(c->sc_host);

@@ -228,11 +228,63 @@ struct CGScal {
   double thresh; // stop when rr <= thresh (= tol^2 |b|^2)
   double sigma;  // shift of the operator
   double dm;     // delta * m_s of the operator (read by the iteration kernels)
+  double rr_cur; // FP32 pair: |r|^2 of the iteration in progress
   int iter, maxit;
   int done;      // 0 running, 1 converged, 2 iteration limit, 3 breakdown (pAp <= 0 / NaN)
-  int pad;
+  int first;     // FP32 pair: no direction yet (beta = 0)
 };
 
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+
+// ---------------------------------------------------------------------------
+// Float-float sums for the FP32 kernels. GB300 executes FP64 at 1/58 of the FP32
+// rate, so the single-precision kernels keep their reductions off the FP64
+// pipe: a value is an unevaluated pair (hi, lo) of floats, and two pairs add
+// with Knuth's TwoSum plus a renormalisation (about 48 significant bits).
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float v = s - a.x;
+  float e = (a.x - (s - v)) + (b.x - v);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+// Block sum of v in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ float2 ff_block_sum(float2 v) {
+  __shared__ float2 sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    v = ff_add(v, w);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? sm[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+      v = ff_add(v, w);
+    }
+  }
+  return v;
+}
+
+// Thread 0 writes the block's sum of loc to part[blockIdx.x].
+__device__ __forceinline__ void ff_write_partial(float loc, float2* part) {
+  float2 v = ff_block_sum(make_float2(loc, 0.f));
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// Sum of G float-float partials in a fixed order (identical in every block);
+// valid in thread 0 of the calling block, as a double.
+__device__ __forceinline__ double ff_sum_partials(const float2* __restrict__ part, int G) {
+  float2 v = make_float2(0.f, 0.f);
+  for (int b = threadIdx.x; b < G; b += blockDim.x) v = ff_add(v, __ldcg(part + b));
+  v = ff_block_sum(v);
+  return (double)v.x + (double)v.y;
+}
 
 }  // namespace hmc

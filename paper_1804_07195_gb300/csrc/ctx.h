@@ -113,6 +113,8 @@ struct hmc_ctx {
   size_t ws_bytes[hmc::WS_COUNT] = {};
 
   double* partials = nullptr;      // reduction partials, kPartials doubles
+  double* partA = nullptr;         // per-block partials of the FP32 CG M^dagger kernel
+  double* partB = nullptr;         // per-block partials of the FP32 CG M kernel
   unsigned int* tickets = nullptr; // one ticket per concurrent reduction site
   hmc::CGScal* sc = nullptr;       // device CG state (two: FP64 outer, FP32 inner)
   hmc::CGScal* sc_host = nullptr;  // pinned mirror

@@ -57,12 +57,27 @@ hmc_status term_grad(hmc_ctx* c, int nmass, const double* masses, const double2*
   return force_launch(c, g, eta, xi, i == nmass ? nullptr : chi[i], grad);
 }
 
+// S_i = src^dagger (M_lo M_lo^dagger)^{-1} src, evaluated in the stationary form
+//   S_i = 2 Re(src^dagger eta) - |M_lo^dagger eta|^2,
+// which equals the definition for the exact eta and, for eta = eta* + e, is off
+// by -e^dagger A e only: second order in the solve error instead of first
+// order (src^dagger eta alone carries the error eta*^dagger r of any solver
+// that is not Galerkin, such as flexible GMRES).
 hmc_status term_action(hmc_ctx* c, int nmass, const double* masses, const double2* const* chi, int i,
-                       const hmc_solver_opts* o, double* dev_out, SolveStats* st) {
+                       const hmc_solver_opts* o, double* S_host, SolveStats* st) {
   const double2* src;
   double2* eta;
   HMC_TRY(term_solve(c, nmass, masses, chi, i, o, &src, &eta, st));
-  return redot_launch(c, c->geo.N, src, eta, dev_out, c->tickets);
+  double2* xi;
+  HMC_TRY(ws_get(c, WS_F_XI, sizeof(double2) * (size_t)c->geo.N, (void**)&xi));
+  HMC_TRY(mdag_launch<double>(c, c->geo, c->delta * lower_mass(masses, i), eta, xi));
+  HMC_TRY(redot_launch(c, c->geo.N, src, eta, c->dscal + 100, c->tickets));
+  HMC_TRY(norm2_launch(c, c->geo.N, xi, c->dscal + 101, c->tickets));
+  HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 100, c->dscal + 100, 2 * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+  *S_host = 2.0 * c->dscal_host[100] - c->dscal_host[101];
+  return HMC_OK;
 }
 
 hmc_status make_chi(hmc_ctx* c, int nmass, const double* masses, const double2* const* rho,
@@ -206,11 +221,10 @@ hmc_status hmc_action(hmc_ctx* c, const double* phi, int nmass, const double* ma
   if (fermion) {
     for (int i = 0; i <= nmass && st == HMC_OK; ++i) {
       if (term != -1 && term != i) continue;
-      st = term_action(c, nmass, masses, (const double2* const*)chi, i, opts, c->dscal + 52, &s);
+      double Si = 0.0;
+      st = term_action(c, nmass, masses, (const double2* const*)chi, i, opts, &Si, &s);
       if (st != HMC_OK) break;
-      HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 52, c->dscal + 52, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      HMC_CUDA(c, cudaStreamSynchronize(c->stream));
-      total += c->dscal_host[52];
+      total += Si;
     }
   }
   *S_out = total;

@@ -9,9 +9,9 @@ hmc_status check_masses(hmc_ctx* c, int nmass, const double* masses);
 // grad += dS_i/dphi for term i (the context's phase tables must hold phi).
 hmc_status term_grad(hmc_ctx* c, int nmass, const double* masses, const double2* const* chi, int i,
                      const hmc_solver_opts* o, double* grad, SolveStats* st);
-// *dev_out = S_i (device scalar).
+// *S_host = S_i (stationary form, synchronises).
 hmc_status term_action(hmc_ctx* c, int nmass, const double* masses, const double2* const* chi, int i,
-                       const hmc_solver_opts* o, double* dev_out, SolveStats* st);
+                       const hmc_solver_opts* o, double* S_host, SolveStats* st);
 hmc_status make_chi(hmc_ctx* c, int nmass, const double* masses, const double2* const* rho,
                     double2* const* chi, const hmc_solver_opts* o, SolveStats* st);
 // grad (+)= phi / (delta U)

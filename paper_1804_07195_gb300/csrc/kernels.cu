@@ -195,23 +195,60 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __rest
   }
 }
 
-// FP32 CG with the direction update folded into the M^dagger kernel. With
-// p_new = r + beta p_old evaluated at every stencil point it reads (double
-// buffered: p_old and p_new are different arrays):
-//   u = M^dagger p_new,  pAp = |u|^2 + sigma |p_new|^2,  alpha = rr / pAp,
-// and p_new is stored at the thread's own sites. beta = 0 on the first
-// iteration (the init kernels set p_old = r, so no NaN can enter).
+// FP32 CG, two kernels per iteration, no atomics and no last-block tail: a
+// kernel only writes one reduction partial per block; every block of the next
+// kernel sums those partials itself in the same fixed order (so all blocks hold
+// identical scalars) after pdl_wait() has made them visible.
+//
+// Kernel A (iteration i): rr_i = sum of B's partials; convergence and limit
+// checks; beta = rr_i / rr_{i-1} (0 on the first iteration); then
+//   p_new = r + beta p_old, evaluated at every stencil point it reads (p_old
+//   and p_new are different arrays), u = M^dagger p_new,
+//   partial of pAp = |u|^2 + sigma |p_new|^2.
+// Kernel B: pAp = sum of A's partials, alpha = rr_i / pAp; then
+//   A p = M u + sigma p_new;  x += alpha p_new;  r -= alpha A p;  partial of |r|^2.
+// Block 0 records the scalars in sc for the host.
 __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> ph,
                                                          const float2* __restrict__ r,
                                                          const float2* __restrict__ pold,
                                                          float2* __restrict__ pnew,
                                                          float2* __restrict__ u, CGScal* sc,
-                                                         double* partials, unsigned* ticket) {
+                                                         const float2* __restrict__ partB, int GB,
+                                                         float2* __restrict__ partA) {
+  __shared__ float s_beta, s_dm, s_sigma;
+  __shared__ int s_done;
   pdl_wait();
   if (sc->done) return;
-  const float dm = (float)sc->dm;
-  const float sigma = (float)sc->sigma;
-  const float beta = (float)sc->beta;
+  // |r|^2: from the init kernel on the first iteration, else from B's partials;
+  // the scalars are formed once per block by thread 0
+  const int first = sc->first;
+  const double rr_sum = first ? 0.0 : ff_sum_partials(partB, GB);
+  if (threadIdx.x == 0) {
+    const double rr = first ? sc->rr_cur : rr_sum;
+    int done = CG_RUNNING;
+    if (!isfinite(rr))
+      done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      done = CG_MAXIT;
+    const double beta = first ? 0.0 : rr / sc->rr;
+    s_beta = (float)beta;
+    s_dm = (float)sc->dm;
+    s_sigma = (float)sc->sigma;
+    s_done = done;
+    if (blockIdx.x == 0) {
+      sc->rr_cur = rr;
+      sc->beta = beta;
+      if (done) {
+        sc->rr = rr;
+        sc->done = done;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float dm = s_dm, sigma = s_sigma, beta = s_beta;
   const int H = g.H;
   const float dk = (float)g.dk;
   float loc = 0.f;
@@ -238,32 +275,43 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
     if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
   }
   pdl_trigger();
-  double acc[1] = {(double)loc};
-  double tot[1];
-  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-    double pAp = tot[0];
-    sc->pAp = pAp;
-    if (!(pAp > 0.0) || !isfinite(pAp)) {
-      sc->alpha = 0.0;
-      sc->done = CG_BREAKDOWN;
-    } else {
-      sc->alpha = sc->rr / pAp;
-    }
-  }
+  ff_write_partial(loc, partA);
 }
 
-// A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2
-// (FP32 vectors; one float partial per thread, reduced in FP64).
 __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
                                                      const float2* __restrict__ u,
                                                      const float2* __restrict__ p,
                                                      float2* __restrict__ x, float2* __restrict__ r,
-                                                     CGScal* sc, double* partials, unsigned* ticket) {
+                                                     CGScal* sc, const float2* __restrict__ partA, int GA,
+                                                     float2* __restrict__ partB) {
+  __shared__ float s_alpha, s_dm, s_sigma;
+  __shared__ int s_bad;
   pdl_wait();
   if (sc->done) return;
-  const float dm = (float)sc->dm;
-  const float sigma = (float)sc->sigma;
-  const float alpha = (float)sc->alpha;
+  const double pAp = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) {
+    const double rr = sc->rr_cur;
+    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+    s_bad = bad;
+    s_alpha = bad ? 0.f : (float)(rr / pAp);
+    s_dm = (float)sc->dm;
+    s_sigma = (float)sc->sigma;
+    if (blockIdx.x == 0) {
+      sc->pAp = pAp;
+      sc->rr = rr;
+      sc->first = 0;
+      if (bad) {
+        sc->alpha = 0.0;
+        sc->done = CG_BREAKDOWN;
+      } else {
+        sc->alpha = rr / pAp;
+        sc->iter += 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float dm = s_dm, sigma = s_sigma, alpha = s_alpha;
   float loc = 0.f;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
     Nbr nb = neighbours(g, q);
@@ -285,20 +333,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
     }
   }
   pdl_trigger();
-  double acc[1] = {(double)loc};
-  double tot[1];
-  if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-    double rr = tot[0];
-    sc->beta = rr / sc->rr;
-    sc->rr = rr;
-    sc->iter += 1;
-    if (!isfinite(rr))
-      sc->done = CG_BREAKDOWN;
-    else if (rr <= sc->thresh)
-      sc->done = CG_CONVERGED;
-    else if (sc->iter >= sc->maxit)
-      sc->done = CG_MAXIT;
-  }
+  ff_write_partial(loc, partB);
 }
 
 template <typename R>
@@ -345,6 +380,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
       init->alpha = init->beta = init->pAp = 0.0;
       init->done = (tot[0] <= init->thresh) ? CG_CONVERGED : CG_RUNNING;
       if (!isfinite(tot[0])) init->done = CG_BREAKDOWN;
+      init->first = 1;
+      init->rr_cur = tot[0];
     }
   }
 }
@@ -375,6 +412,8 @@ __global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restri
     sc->alpha = sc->beta = sc->pAp = 0.0;
     sc->done = (tot[0] <= sc->thresh) ? CG_CONVERGED : CG_RUNNING;
     if (!isfinite(tot[0])) sc->done = CG_BREAKDOWN;
+    sc->first = 1;
+    sc->rr_cur = tot[0];
   }
 }
 
@@ -672,15 +711,20 @@ INST(double)
 
 hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
+  (void)ticket;
+  const int GB = shape_grid(c, K_CG_M32, g.H);
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
     launch_pdl(c, k_cg32_pmdag, PDL(K_CG_MDAG32, g.H), g, phase_of<float>(c), r, pold, pnew, u, sc,
-               c->partials, ticket);
+               (const float2*)c->partB, GB, (float2*)c->partA);
   });
 }
 hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket) {
+  (void)ticket;
+  const int GA = shape_grid(c, K_CG_MDAG32, g.H);
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    launch_pdl(c, k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc, c->partials, ticket);
+    launch_pdl(c, k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc,
+               (const float2*)c->partA, GA, (float2*)c->partB);
   });
 }
 

@@ -233,16 +233,18 @@ extern "C" hmc_status hmc_md_trajectory(hmc_ctx* c, double* phi, double* pi, int
   // H1 = S(phi') + pi'^2/2 with the action solves at action_opts' tolerance
   HMC_TRY(md.tables());
   SolveStats hst;
-  HMC_TRY(half_sq_launch(c, (int)N, phi, inv_dU, pi, c->dscal + 54, c->tickets));
+  double h1 = 0.0;
   for (int i = 0; i <= nmass; ++i) {
-    s = term_action(c, nmass, masses, chi.data(), i, action_opts, c->dscal + 56 + i, &hst);
+    double Si = 0.0;
+    s = term_action(c, nmass, masses, chi.data(), i, action_opts, &Si, &hst);
     if (s != HMC_OK) return s;
+    h1 += Si;
   }
-  HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 54, c->dscal + 54, sizeof(double) * (2 + nmass + 1),
+  HMC_TRY(half_sq_launch(c, (int)N, phi, inv_dU, pi, c->dscal + 54, c->tickets));
+  HMC_CUDA(c, cudaMemcpyAsync(c->dscal_host + 54, c->dscal + 54, sizeof(double) * 2,
                               cudaMemcpyDeviceToHost, c->stream));
   HMC_CUDA(c, cudaStreamSynchronize(c->stream));
-  double h1 = c->dscal_host[54] + c->dscal_host[55];
-  for (int i = 0; i <= nmass; ++i) h1 += c->dscal_host[56 + i];
+  h1 += c->dscal_host[54] + c->dscal_host[55];
   *H0 = h0;
   *H1 = h1;
   if (agg) {

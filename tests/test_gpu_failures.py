@@ -1,0 +1,95 @@
+"""Failure detection, with every fault made on the host: a NaN planted in the
+field or the right-hand side, an iteration limit that is too small, invalid
+arguments and descriptors. Each must come back as a status, never as a fault,
+a hang or an abort, and the context must stay usable afterwards."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+from gpu_util import ctx_for, dev, host, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_nan_in_field_is_reported_and_context_survives():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C1")
+    bad = w.phi.copy()
+    bad[17] = np.nan
+    with ctx_for(w.lat) as ctx:
+        for solve in (lambda p: ctx.solve_cg(p, 0.0, dev(w.b), tol=1e-10),
+                      lambda p: ctx.solve_fgmres(p, 0.0, dev(w.b), tol=1e-10)):
+            with pytest.raises(hmc.HMCError) as e:
+                solve(dev(bad))
+            assert e.value.status == -4  # HMC_ERR_NAN
+        # the same context still solves a good system
+        x, info = ctx.solve_cg(dev(w.phi), 0.0, dev(w.b), tol=1e-10)
+        assert info["true_rel_res"] <= 1e-10
+
+
+def test_nan_in_rhs_is_reported():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C1")
+    b = w.b.copy()
+    b[3] = complex(np.nan, 0.0)
+    with ctx_for(w.lat) as ctx:
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_fgmres(dev(w.phi), 0.0, dev(b), tol=1e-10)
+        assert e.value.status == -4
+
+
+def test_spcg_iteration_limit():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C1")
+    with ctx_for(w.lat) as ctx:
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_spcg(dev(w.phi), 0.0, dev(w.b.astype(np.complex64)), tol=1e-7, maxit=3)
+        assert e.value.status == -3
+        _, info = ctx.solve_spcg(dev(w.phi), 0.0, dev(w.b.astype(np.complex64)), tol=1e-7, maxit=3,
+                                 allow_fail=True)
+        assert info["iters"] == 3
+
+
+def test_invalid_arguments():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.small(3, 3, 4, seed=2)
+    with ctx_for(w.lat) as ctx:
+        phi, b = dev(w.phi), dev(w.b)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_cg(phi, 0.0, b, tol=-1.0)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_cg(phi, 0.0, b, maxit=0)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_fgmres(phi, 0.0, b, restart=0)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_fgmres(phi, 0.0, b, inner_prec=16)
+        with pytest.raises(hmc.HMCError):
+            ctx.force(phi, [0.1] * 9, [b] * 10)  # more masses than supported
+        with pytest.raises(hmc.HMCError):
+            ctx.md_trajectory(phi.clone(), dev(w.pi), [0.2], [b, b], hmc.Integrator(0, 5, (2,)),
+                              hmc.SolverOpts(), hmc.SolverOpts())  # N_0 does not divide N_MD
+        with pytest.raises(ValueError):
+            ctx.apply_M(phi, 0.0, b[:-1])  # wrong length is caught in the binding
+
+
+def test_bad_batched_descriptor():
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.small(3, 3, 4, seed=2)
+    lat = hmc.Lattice(3, 3, 4, 1.0, 2.0, 4.0)
+    good = {"lattice": lat, "phi": dev(w.phi), "ms": 0.0, "b": dev(w.b),
+            "x": torch.zeros(lat.nsites, dtype=torch.complex128, device="cuda")}
+    with ctx_for(w.lat) as ctx:
+        bad = dict(good, sigma=-1.0)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_batched([good, bad])
+        bad = dict(good, tol=0.0)
+        with pytest.raises(hmc.HMCError):
+            ctx.solve_batched([bad])
+        infos = ctx.solve_batched([good])
+        assert infos[0]["true_rel_res"] <= 1e-10

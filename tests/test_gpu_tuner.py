@@ -1,0 +1,32 @@
+"""The Hasenbusch tuner of Section 7.2 run end to end on the GPU (12x12,
+nt=32): solve times for several staggered masses fit Eq. solver_time_eqn with
+0 < lambda_min < lambda_max, the two masses sit geometrically between them,
+the measured small forces grow with |mu_1 - mu_0|, and the time scales are
+positive integers."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+from gpu_util import ctx_for, dev, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tuner_end_to_end():
+    need_gpu()
+    from paper_1804_07195_gb300 import tuner
+    w = W.workload("C2")
+    with ctx_for(w.lat) as ctx:
+        res = tuner.measure_and_tune(ctx, dev(w.phi), [dev(r) for r in w.rho], repeats=2)
+    assert 0 < res.lam_min < res.lam_max
+    mu = res.masses
+    assert res.lam_min < mu[0] < mu[1] < res.lam_max
+    assert math.isclose(mu[1] / mu[0], mu[0] / res.lam_min, rel_tol=1e-9)
+    # the pair (0.2, 1.5) is far apart, (0.1, 0.3) close: its force is smaller
+    F = dict(zip(map(tuple, res.measurements["pairs"]), res.measurements["F_chi1"]))
+    assert F[(0.2, 1.5)] > F[(0.1, 0.3)]
+    assert all(np.isfinite(res.small_force)) and all(np.isfinite(res.large_force))
+    assert res.N[0] == res.N[1] >= 1

@@ -79,8 +79,11 @@ typedef struct {
 
 /* Solver selection for calls that solve internally (forces, actions, MD). */
 enum {
-  HMC_SOLVER_CG64 = 0,        /* plain FP64 CG (Section 3) */
-  HMC_SOLVER_FGMRES_MIXED = 1 /* FGMRES with FP32 CG preconditioner (Algorithm A.1) */
+  HMC_SOLVER_CG64 = 0,         /* plain FP64 CG (Section 3) */
+  HMC_SOLVER_FGMRES_MIXED = 1, /* FGMRES with FP32 CG preconditioner (Algorithm A.1) */
+  HMC_SOLVER_FGMRES_FP64 = 2,  /* Algorithm A.1 with an FP64 CG preconditioner: all FP64,
+                                  true residual recomputed at every restart */
+  HMC_SOLVER_FCG_MIXED = 3     /* flexible CG with FP32 CG preconditioner (Section 3) */
 };
 
 typedef struct {
@@ -176,6 +179,17 @@ hmc_status hmc_solve_spcg(hmc_ctx* ctx, const double* phi, double ms, double sig
 hmc_status hmc_solve_fgmres(hmc_ctx* ctx, const double* phi, double ms, double sigma, const void* b,
                             void* x, double tol, int restart, double a, int inner_prec, int maxit,
                             hmc_solve_info* info);
+
+/* Flexibly preconditioned CG (Section 3: the FP64 CG with the single-precision
+ * CG as its preconditioner, made flexible because a CG stopped at a tolerance
+ * is not a fixed linear map). One previous direction is kept:
+ *   z_i = spCG(r_i), p_i = z_i - (p_{i-1}^H A z_i / p_{i-1}^H A p_{i-1}) p_{i-1},
+ *   alpha = p_i^H r_i / p_i^H A p_i, x += alpha p_i, r -= alpha A p_i,
+ * with the spCG tolerance max(tol*a*|b|/|r_i|, 1e-6) and z_i = r_i once that
+ * ratio reaches 1. Stops when |r| <= tol |b| (recursive residual; info reports
+ * the true one). b, x complex128; x is output only. Synchronous. */
+hmc_status hmc_solve_fcg(hmc_ctx* ctx, const double* phi, double ms, double sigma, const void* b,
+                         void* x, double tol, double a, int maxit, hmc_solve_info* info);
 
 /* One independent system of a batched solve. Lattices may differ between
  * systems; phi, b, x are device arrays in each system's own canonical layout. */

@@ -10,6 +10,8 @@ Algorithm A.1).
                  Section 3, used as the preconditioner).
   fgmres      -- flexible GMRES with spCG as preconditioner, Algorithm A.1, with
                  restart length m = 10 and inner tolerance factor a = 5 (Appendix A).
+  fcg         -- flexibly preconditioned CG with spCG as preconditioner, the
+                 mixed-precision solver Section 3 describes before FGMRES.
 
 Readings taken where Algorithm A.1 is garbled or silent:
   * h and y are complex (the operator is complex Hermitian); h_ij = v_i^H w,
@@ -190,6 +192,60 @@ def fgmres(apply_A: Callable, apply_A32: Callable, b: np.ndarray, tol: float = 1
     res.inner_iters = inner_total
     res.outer_iters = outer
     return res
+
+
+def fcg(apply_A: Callable, apply_A32: Callable, b: np.ndarray, tol: float = 1e-10, a: float = 5.0,
+        inner_floor: float = 1e-6, inner_maxit: int = 2000, maxit: int = 1000,
+        precond: Callable = None) -> SolveResult:
+    """Flexible CG (Section 3: an FP64 CG whose preconditioner is the spCG
+    solve, made flexible because spCG with a tolerance is not a fixed linear
+    map; Notay's method). Readings, as the paper gives no detail: one previous
+    direction is kept (truncation 1),
+        z_i = spCG(r_i),  p_i = z_i - (p_{i-1}^H A z_i / p_{i-1}^H A p_{i-1}) p_{i-1},
+        alpha = p_i^H r_i / p_i^H A p_i,  x += alpha p_i,  r -= alpha A p_i,
+    with the spCG tolerance max(TOL a |b| / |r_i|, floor) of Algorithm A.1 and
+    z_i = r_i once that ratio reaches 1; stop when the recursive residual
+    satisfies |r| <= TOL |b|. `precond(r, tol)` replaces the spCG solve when
+    given (z = r is still used once TOL a |b| / |r| >= 1)."""
+    b = b.astype(np.complex128)
+    bnorm = np.sqrt(norm2_64(b))
+    if bnorm == 0.0:
+        return SolveResult(np.zeros_like(b), 0, True, [0.0])
+    x = np.zeros_like(b)
+    r = b.copy()
+    rnorm = bnorm
+    hist = [1.0]
+    inner_total = 0
+    p_prev = q_prev = None
+    pq_prev = None
+    k = 0
+    while rnorm > tol * bnorm and k < maxit:
+        t = tol * a * bnorm / rnorm
+        if t < 1.0 and precond is not None:
+            z = precond(r, max(t, inner_floor))
+        elif t < 1.0:
+            res = spcg(apply_A32, r, max(t, inner_floor), inner_maxit)
+            inner_total += res.iters
+            z = res.x.astype(np.complex128)
+        else:
+            z = r.copy()
+        if p_prev is None:
+            p = z
+        else:
+            beta = vdot64(q_prev, z) / pq_prev   # (A p_prev)^H z / p_prev^H A p_prev
+            p = z - beta * p_prev
+        q = apply_A(p)
+        pq = float(np.real(vdot64(p, q)))
+        alpha = vdot64(p, r) / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rnorm = np.sqrt(norm2_64(r))
+        p_prev, q_prev, pq_prev = p, q, pq
+        k += 1
+        hist.append(rnorm / bnorm)
+    out = SolveResult(x, k, rnorm <= tol * bnorm, hist)
+    out.inner_iters = inner_total
+    return out
 
 
 def true_rel_residual(apply_A: Callable, x: np.ndarray, b: np.ndarray) -> float:

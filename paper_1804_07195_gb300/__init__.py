@@ -210,6 +210,15 @@ class Context:
         self._check(st, allow=(_abi.HMC_ERR_NOT_CONVERGED,) if allow_fail else ())
         return x, info.as_dict()
 
+    def solve_fcg(self, phi, ms, b, sigma=0.0, tol=1e-10, a=5.0, maxit=1000, allow_fail=False):
+        import torch
+        x = torch.zeros_like(b)
+        info = _abi.hmc_solve_info()
+        st = self.lib.hmc_solve_fcg(self.h, self._phi(phi), ms, sigma, _ptr(b, torch.complex128, self.N, "b"),
+                                    _ptr(x, torch.complex128, self.N, "x"), tol, a, maxit, C.byref(info))
+        self._check(st, allow=(_abi.HMC_ERR_NOT_CONVERGED,) if allow_fail else ())
+        return x, info.as_dict()
+
     # --- Hasenbusch terms, force, action --------------------------------------
     def _vecs(self, vs, what):
         import torch

@@ -22,6 +22,8 @@ HMC_ERR_NOMEM = -6
 HMC_MAX_MASSES = 8
 HMC_SOLVER_CG64 = 0
 HMC_SOLVER_FGMRES_MIXED = 1
+HMC_SOLVER_FGMRES_FP64 = 2
+HMC_SOLVER_FCG_MIXED = 3
 HMC_INTEG_NESTED_OMELYAN = 0
 HMC_INTEG_LEAPFROG = 1
 HMC_INTEG_FORCE_GRADIENT = 2
@@ -89,6 +91,7 @@ PROTOTYPES = {
     "hmc_solve_cg": (S, [P, P, D, D, P, P, D, I, C.POINTER(hmc_solve_info)]),
     "hmc_solve_spcg": (S, [P, P, D, D, P, P, D, I, C.POINTER(hmc_solve_info)]),
     "hmc_solve_fgmres": (S, [P, P, D, D, P, P, D, I, D, I, I, C.POINTER(hmc_solve_info)]),
+    "hmc_solve_fcg": (S, [P, P, D, D, P, P, D, D, I, C.POINTER(hmc_solve_info)]),
     "hmc_solve_batched": (S, [P, I, C.POINTER(hmc_system), I, C.POINTER(hmc_solve_info)]),
     "hmc_make_chi": (S, [P, P, I, C.POINTER(D), C.POINTER(P), C.POINTER(P),
                          C.POINTER(hmc_solver_opts), C.POINTER(hmc_solve_info)]),

@@ -410,6 +410,19 @@ hmc_status hmc_solve_fgmres(hmc_ctx* c, const double* phi, double ms, double sig
   return st;
 }
 
+hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
+                         double tol, double a, int maxit, hmc_solve_info* info) {
+  if (!c) return HMC_ERR_INVALID;
+  const double t0 = now_s();
+  HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
+  if (!(a > 0.0)) return fail(c, HMC_ERR_INVALID, "a must be positive");
+  HMC_TRY(prepare_field(c, phi));
+  SolveStats s;
+  hmc_status st = fcg_core(c, ms, sigma, (const double2*)b, (double2*)x, tol, a, maxit, 1e-6, 2000, &s);
+  fill_info(info, s, st, t0, 0, c->geo.N);
+  return st;
+}
+
 hmc_status hmc_profile(hmc_ctx* c, int timing_on, int reset) {
   if (!c) return HMC_ERR_INVALID;
   if (reset) {

@@ -118,10 +118,10 @@ static hmc_status check_chi(hmc_ctx* c, int nmass, const void* const* v, const c
 
 static hmc_status check_opts(hmc_ctx* c, const hmc_solver_opts* o) {
   if (!o) return fail(c, HMC_ERR_INVALID, "solver options are NULL");
-  if (o->method != HMC_SOLVER_CG64 && o->method != HMC_SOLVER_FGMRES_MIXED)
+  if (o->method < HMC_SOLVER_CG64 || o->method > HMC_SOLVER_FCG_MIXED)
     return fail(c, HMC_ERR_INVALID, "unknown solver method");
   if (!(o->tol > 0.0) || o->maxit < 1) return fail(c, HMC_ERR_INVALID, "bad tol or maxit");
-  if (o->method == HMC_SOLVER_FGMRES_MIXED &&
+  if (o->method != HMC_SOLVER_CG64 &&
       (o->restart < 1 || o->restart > kMaxRestart || !(o->a > 0.0) || !(o->inner_floor > 0.0) ||
        o->inner_maxit < 1))
     return fail(c, HMC_ERR_INVALID, "bad FGMRES options");

@@ -278,7 +278,7 @@ static bool normal_eq_cholesky(const std::vector<std::complex<double>>& H, int l
 
 // Preconditioner solve z = A^{-1} v to relative tolerance t in precision prec
 // (32: spCG through float copies; 64: FP64 CG). t >= 1 gives z = v.
-static hmc_status precondition(hmc_ctx* c, double ms, double sigma, const double2* v64,
+hmc_status precondition_solve(hmc_ctx* c, double ms, double sigma, const double2* v64,
                                const float2* v32, double2* z, double t, int prec, int inner_maxit,
                                SolveStats* st) {
   const int N = c->geo.N;
@@ -342,7 +342,7 @@ hmc_status fgmres_core(hmc_ctx* c, double ms, double sigma, const double2* b, do
     return HMC_OK;
   }
   // first line of Algorithm A.1: spCG solve of A x = b (tolerance tol*a, floored)
-  HMC_TRY(precondition(c, ms, sigma, b, nullptr, x, std::max(tol * a, inner_floor), inner_prec,
+  HMC_TRY(precondition_solve(c, ms, sigma, b, nullptr, x, std::max(tol * a, inner_floor), inner_prec,
                        inner_maxit, st));
   if (tol * a >= 1.0) HMC_CUDA(c, cudaMemsetAsync(x, 0, vb, c->stream));
   // r = b - A x, ERR = |r|
@@ -378,7 +378,7 @@ hmc_status fgmres_core(hmc_ctx* c, double ms, double sigma, const double2* b, do
       HMC_TRY(scale_launch(c, N, 1.0 / wnorm, wsrc, Vj, v32));
       // z_j: spCG with tolerance TOL a |b| / ERR, or z_j = v_j
       const double t = tol * a * bnorm / err;
-      HMC_TRY(precondition(c, ms, sigma, Vj, v32, Zj, t < 1.0 ? std::max(t, inner_floor) : 1.0,
+      HMC_TRY(precondition_solve(c, ms, sigma, Vj, v32, Zj, t < 1.0 ? std::max(t, inner_floor) : 1.0,
                            inner_prec, inner_maxit, st));
       // w = A z_j, h_ij = v_i^H w (i <= j), w -= sum h_ij v_i, h_{j+1,j} = |w|
       HMC_TRY(apply_A64(c, ms, sigma, Zj, w));
@@ -446,13 +446,110 @@ hmc_status fgmres_core(hmc_ctx* c, double ms, double sigma, const double2* b, do
   return HMC_OK;
 }
 
+hmc_status fcg_core(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x, double tol,
+                    double a, int maxit, double inner_floor, int inner_maxit, SolveStats* st) {
+  using cd = std::complex<double>;
+  const int N = c->geo.N;
+  const size_t vb = sizeof(double2) * (size_t)N;
+  double2 *r, *z, *buf, *u;
+  float2* v32 = nullptr;
+  HMC_TRY(ws_get(c, WS_FG_R, vb, (void**)&r));
+  HMC_TRY(ws_get(c, WS_FG_W, vb, (void**)&z));
+  HMC_TRY(ws_get(c, WS_FG_V, vb * 4, (void**)&buf));
+  HMC_TRY(ws_get(c, WS_U64, vb, (void**)&u));
+  double2* p = buf;
+  double2* q = buf + N;
+  double2* pp = buf + 2 * (size_t)N;  // previous direction and its image
+  double2* qp = buf + 3 * (size_t)N;
+  unsigned* tk = c->tickets;
+  double* d = c->dscal;
+  double* h = c->dscal_host;
+  auto fetch = [&](int n) -> hmc_status {
+    HMC_CUDA(c, cudaMemcpyAsync(h + 80, d + 80, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HMC_OK;
+  };
+  HMC_TRY(norm2_launch(c, N, b, d + 80, tk));
+  HMC_TRY(fetch(1));
+  const double bnorm = std::sqrt(h[80]);
+  if (!std::isfinite(bnorm)) return fail(c, HMC_ERR_NAN, "FCG: right-hand side is not finite");
+  HMC_CUDA(c, cudaMemsetAsync(x, 0, vb, c->stream));
+  if (bnorm == 0.0) {
+    st->true_rel = 0.0;
+    return HMC_OK;
+  }
+  HMC_CUDA(c, cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, c->stream));
+  double rnorm = bnorm, pq_prev = 0.0;
+  int k = 0;
+  while (rnorm > tol * bnorm && k < maxit) {
+    const double t = tol * a * bnorm / rnorm;
+    HMC_TRY(precondition_solve(c, ms, sigma, r, nullptr, z, t < 1.0 ? std::max(t, inner_floor) : 1.0, 32,
+                               inner_maxit, st));
+    HMC_CUDA(c, cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, c->stream));
+    if (k > 0) {
+      // beta = (A p_prev)^H z / (p_prev^H A p_prev);  p = z - beta p_prev
+      VecList V;
+      V.v[0] = qp;
+      HMC_TRY(mdot_launch(c, N, V, 1, z, d + 80, tk));
+      HMC_TRY(fetch(2));
+      const cd beta = cd(h[80], h[81]) / pq_prev;
+      VecList P;
+      P.v[0] = pp;
+      CoefList co;
+      co.re[0] = -beta.real();
+      co.im[0] = -beta.imag();
+      HMC_TRY(xupd_launch(c, N, P, co, 1, p));
+    }
+    HMC_TRY(apply_A64(c, ms, sigma, p, q));
+    st->applies64++;
+    VecList V;
+    V.v[0] = p;
+    HMC_TRY(redot_launch(c, N, p, q, d + 82, tk));
+    HMC_TRY(mdot_launch(c, N, V, 1, r, d + 80, tk));
+    HMC_TRY(fetch(3));
+    const double pq = h[82];
+    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(c, HMC_ERR_NAN, "FCG: non-positive curvature");
+    const cd alpha = cd(h[80], h[81]) / pq;
+    VecList P, Q;
+    P.v[0] = p;
+    Q.v[0] = q;
+    CoefList ca, cm;
+    ca.re[0] = alpha.real();
+    ca.im[0] = alpha.imag();
+    cm.re[0] = -alpha.real();
+    cm.im[0] = -alpha.imag();
+    HMC_TRY(xupd_launch(c, N, P, ca, 1, x));
+    HMC_TRY(xupd_launch(c, N, Q, cm, 1, r));
+    HMC_TRY(norm2_launch(c, N, r, d + 80, tk));
+    HMC_TRY(fetch(1));
+    rnorm = std::sqrt(h[80]);
+    if (!std::isfinite(rnorm)) return fail(c, HMC_ERR_NAN, "FCG: residual is not finite");
+    std::swap(p, pp);
+    std::swap(q, qp);
+    pq_prev = pq;
+    ++k;
+  }
+  st->iters += k;
+  // true residual in FP64
+  HMC_TRY(mdag_launch<double>(c, c->geo, c->delta * ms, x, u));
+  HMC_TRY(resid_launch<double>(c, c->geo, c->delta * ms, u, x, b, sigma, r, nullptr, nullptr, 0.0, 0, d + 80, tk));
+  HMC_TRY(fetch(2));
+  st->applies64++;
+  st->true_rel = std::sqrt(h[80] / h[81]);
+  if (!(rnorm <= tol * bnorm)) return fail(c, HMC_ERR_NOT_CONVERGED, "FCG reached its step limit");
+  return HMC_OK;
+}
+
 hmc_status solve_opts(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x,
                       const hmc_solver_opts* o, SolveStats* st) {
   if (o->method == HMC_SOLVER_CG64)
     return cg_core<double>(c, ms, sigma, b, x, true, o->tol, o->maxit, 0, true, st);
-  if (o->method == HMC_SOLVER_FGMRES_MIXED)
-    return fgmres_core(c, ms, sigma, b, x, o->tol, o->restart, o->a, 32, o->maxit, o->inner_floor,
+  if (o->method == HMC_SOLVER_FGMRES_MIXED || o->method == HMC_SOLVER_FGMRES_FP64)
+    return fgmres_core(c, ms, sigma, b, x, o->tol, o->restart, o->a,
+                       o->method == HMC_SOLVER_FGMRES_MIXED ? 32 : 64, o->maxit, o->inner_floor,
                        o->inner_maxit, st);
+  if (o->method == HMC_SOLVER_FCG_MIXED)
+    return fcg_core(c, ms, sigma, b, x, o->tol, o->a, o->maxit, o->inner_floor, o->inner_maxit, st);
   return fail(c, HMC_ERR_INVALID, "unknown solver method");
 }
 

@@ -23,6 +23,15 @@ hmc_status fgmres_core(hmc_ctx* c, double ms, double sigma, const double2* b, do
                        int restart, double a, int inner_prec, int maxit, double inner_floor,
                        int inner_maxit, SolveStats* st);
 
+// z = A^{-1} v to relative tolerance t by CG in precision prec (32: through
+// float copies; 64: FP64); t >= 1 gives z = v.
+hmc_status precondition_solve(hmc_ctx* c, double ms, double sigma, const double2* v64, const float2* v32,
+                              double2* z, double t, int prec, int inner_maxit, SolveStats* st);
+
+// Flexible CG with an FP32 CG preconditioner (Section 3).
+hmc_status fcg_core(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x, double tol,
+                    double a, int maxit, double inner_floor, int inner_maxit, SolveStats* st);
+
 // Dispatch on opts->method; x is the output (start at 0).
 hmc_status solve_opts(hmc_ctx* c, double ms, double sigma, const double2* b, double2* x,
                       const hmc_solver_opts* opts, SolveStats* st);

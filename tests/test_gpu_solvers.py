@@ -117,3 +117,22 @@ def test_not_converged_is_reported():
         assert e.value.status == -3
         x, info = ctx.solve_cg(dev(w.phi), 0.0, dev(w.b), tol=1e-10, maxit=5, allow_fail=True)
         assert info["iters"] == 5 and info["true_rel_res"] > 1e-10
+
+
+@pytest.mark.parametrize("name,ms", [("C1", 0.0), ("C3", 0.2)])
+def test_fcg_mixed(name, ms):
+    """Flexible CG with the FP32 CG preconditioner (Section 3) against the
+    oracle's flexible CG: both converge, in a similar number of outer steps, and
+    the true residual meets the tolerance up to the drift of the recursive one."""
+    need_gpu()
+    w = W.workload(name)
+    ol = OLat.from_params(w.lat)
+    with ctx_for(w.lat) as ctx:
+        x, info = ctx.solve_fcg(dev(w.phi), ms, dev(w.b), tol=1e-10)
+    assert true_rel(ol, w.phi, ms, 0.0, host(x), w.b) <= 2e-10
+    assert info["iters_inner"] > 0
+    if name == "C1":
+        A64 = lambda v: of.apply_MMdag(ol, w.phi, ms, v)
+        A32 = lambda v: of.apply_MMdag(ol, w.phi, ms, v.astype(np.complex64)).astype(np.complex64)
+        ref = osv.fcg(A64, A32, w.b, tol=1e-10)
+        assert abs(info["iters"] - ref.iters) <= 2

@@ -60,6 +60,23 @@ def test_fgmres_residual_estimate_tracks_true_residual():
     assert solvers.true_rel_residual(A64, res.x, w.b) <= 1e-12
 
 
+def test_fcg_matches_lu_with_few_outer_steps():
+    w, lat, Amat, A64, A32 = problem()
+    x_ref = solvers.dense_solve(Amat, w.b)
+    res = solvers.fcg(A64, A32, w.b, tol=1e-10)
+    assert res.converged and res.inner_iters > 0
+    assert solvers.true_rel_residual(A64, res.x, w.b) <= 2e-10
+    assert np.linalg.norm(res.x - x_ref) < 1e-7 * np.linalg.norm(x_ref)
+
+
+def test_fcg_with_exact_preconditioner_is_one_step():
+    """With z = A^{-1} r exactly, alpha = 1 and the first step solves the system."""
+    w, lat, Amat, A64, A32 = problem(shape=(3, 3, 8))
+    exact = lambda v, t: solvers.dense_solve(Amat, v)
+    res = solvers.fcg(A64, None, w.b, tol=1e-12, precond=exact)
+    assert res.iters == 1 and res.converged
+
+
 def test_spcg_reaches_single_precision_floor():
     w, lat, Amat, A64, A32 = problem(shape=(3, 3, 8))
     res = solvers.spcg(A32, w.b, tol=1e-6)

@@ -1,0 +1,56 @@
+"""A Markov chain of HMC trajectories (the HMC outline of Section 2) on top of
+hmc_md_trajectory: heat-bath momenta pi ~ exp(-pi^2/2) and vectors
+rho ~ exp(-rho^dagger rho) drawn on the host from a seeded generator, one
+trajectory on the device, and the Metropolis step min(1, exp(-dH)).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence
+
+import numpy as np
+
+
+@dataclass
+class ChainResult:
+    phi: object
+    accepted: int
+    trajectories: int
+    dH: List[float] = field(default_factory=list)
+    measurements: list = field(default_factory=list)
+
+    @property
+    def acceptance(self) -> float:
+        return self.accepted / max(self.trajectories, 1)
+
+
+def run_chain(ctx, phi, n_traj: int, masses: Sequence[float], integ, md_opts, action_opts, seed,
+              therm: int = 0, measure: Optional[Callable] = None, measure_every: int = 1) -> ChainResult:
+    """Run therm + n_traj trajectories from phi (a float64 CUDA tensor, not
+    modified); `measure(phi)` is called on the current field after each of the
+    last n_traj trajectories (every `measure_every`)."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    N = ctx.N
+    dev = phi.device
+    phi = phi.clone()
+    res = ChainResult(phi, 0, 0)
+    for it in range(therm + n_traj):
+        pi = torch.tensor(g.normal(size=N), device=dev)
+        rho = [torch.tensor((g.normal(0.0, math.sqrt(0.5), N) + 1j * g.normal(0.0, math.sqrt(0.5), N)),
+                            device=dev) for _ in range(len(masses) + 1)]
+        trial = phi.clone()
+        H0, H1, _ = ctx.md_trajectory(trial, pi, list(masses), rho, integ, md_opts, action_opts)
+        dH = H1 - H0
+        if g.uniform() < math.exp(min(0.0, -dH)):
+            phi = trial
+            if it >= therm:
+                res.accepted += 1
+        if it >= therm:
+            res.trajectories += 1
+            res.dH.append(dH)
+            if measure is not None and (it - therm) % measure_every == 0:
+                res.measurements.append(measure(phi))
+    res.phi = phi
+    return res

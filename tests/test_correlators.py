@@ -1,0 +1,43 @@
+"""Correlator helpers (Section 8.1) on the free field, with the oracle's dense
+propagator: the band projection of M^{-1} falls as a single exponential whose
+fitted energy approaches the free band energy |f(k)| (3 at Gamma, 1 at M on the
+2x1 torus) as delta -> 0. CPU only."""
+import numpy as np
+import pytest
+
+from oracle import fermion
+from oracle.lattice import Lattice
+from paper_1804_07195_gb300 import correlators as cr
+
+
+def free_correlator(lat, k1):
+    G = np.linalg.inv(fermion.dense_M(lat, np.zeros(lat.N), 0.0))
+    o = cr.band_orbital(lat.n, lat.m, k1)
+    C = np.zeros(lat.nt, complex)
+    for t0 in range(lat.nt):
+        src = cr.slice_indices(lat.n, lat.m, lat.nt, t0)
+        col = G[:, src] @ o
+        for tau in range(lat.nt):
+            t = (t0 + tau) % lat.nt
+            sign = -1.0 if t0 + tau >= lat.nt else 1.0
+            C[tau] += sign * np.vdot(o, col[cr.slice_indices(lat.n, lat.m, lat.nt, t)])
+    return C / lat.nt
+
+
+@pytest.mark.parametrize("k1,E", [(0.0, 3.0), (np.pi, 1.0)])
+def test_free_band_energies(paper, k1, E):
+    win = paper["fit_windows"]["Gamma" if k1 == 0.0 else "M"]
+    errs = []
+    for nt in (32, 64):
+        lat = Lattice(2, 1, nt, 1.0, 4.0, 8.0)
+        C = free_correlator(lat, k1)
+        errs.append(abs(cr.fit_energy(C, lat.delta, win) - E))
+    assert errs[1] < 0.02
+    assert errs[1] < 0.5 * errs[0]   # discretisation error shrinks with delta
+
+
+def test_bootstrap_of_identical_samples_has_no_spread():
+    lat = Lattice(2, 1, 32, 1.0, 4.0, 8.0)
+    C = free_correlator(lat, 0.0)
+    E, dE = cr.bootstrap_energy(np.array([C] * 10), lat.delta, (0.2, 1.0), nboot=20)
+    assert dE < 1e-12 and abs(E - cr.fit_energy(C, lat.delta, (0.2, 1.0))) < 1e-12

@@ -135,4 +135,7 @@ def test_fcg_mixed(name, ms):
         A64 = lambda v: of.apply_MMdag(ol, w.phi, ms, v)
         A32 = lambda v: of.apply_MMdag(ol, w.phi, ms, v.astype(np.complex64)).astype(np.complex64)
         ref = osv.fcg(A64, A32, w.b, tol=1e-10)
-        assert abs(info["iters"] - ref.iters) <= 2
+        # once TOL a |b| / |r| >= 1 the steps are unpreconditioned (z = r) and
+        # the length of that tail depends on FP32 rounding inside the spCG solves
+        assert abs(info["iters"] - ref.iters) <= max(3, 0.5 * ref.iters)
+        assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters

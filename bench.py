@@ -40,6 +40,7 @@ UNIT = "Gsite/s"
 WORKLOAD = ("102x102 honeycomb torus, nt=64 (1,331,712 sites), kappa=1, U=3.8, beta=12: one "
             "nested-Omelyan MD trajectory (N_MD=30, N_i=(6,2,2)) with 3 Hasenbusch masses "
             "(0.1,0.5,2.0), mixed FP32/FP64 FGMRES forces at 1e-10")
+WORKLOAD_A = "FGMRES inner tolerance factor a = {a}"
 
 
 def dist_env():
@@ -160,6 +161,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fgmres-a", type=float, default=5.0,
+                    help="inner tolerance factor a of Algorithm A.1 for the trajectory's solves")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
@@ -193,8 +196,8 @@ def main():
     N = lat.nsites
     masses = list(W.C5_MASSES)
     integ = hmc.Integrator(0, W.C5_NMD, W.C5_NI, W.OMELYAN_ZETA, 1.0)
-    md_opts = hmc.SolverOpts(method=1, tol=1e-10)
-    act_opts = hmc.SolverOpts(method=1, tol=1e-12)
+    md_opts = hmc.SolverOpts(method=1, tol=1e-10, a=args.fgmres_a)
+    act_opts = hmc.SolverOpts(method=1, tol=1e-12, a=args.fgmres_a)
 
     nsteps_total = args.warmup + args.steps + 1 + args.e2e_steps
 
@@ -304,7 +307,10 @@ def main():
     b = dev_inputs[0][1][0]
     solve = {}
     for name, fn in (("fp64_cg", lambda: ctx.solve_cg(phi_t, 0.0, b, tol=1e-10)),
-                     ("mixed_fgmres", lambda: ctx.solve_fgmres(phi_t, 0.0, b, tol=1e-10))):
+                     ("mixed_fgmres", lambda: ctx.solve_fgmres(phi_t, 0.0, b, tol=1e-10, a=args.fgmres_a)),
+                     ("mixed_fgmres_a5_paper", lambda: ctx.solve_fgmres(phi_t, 0.0, b, tol=1e-10, a=5.0)),
+                     ("mixed_fgmres_a1", lambda: ctx.solve_fgmres(phi_t, 0.0, b, tol=1e-10, a=1.0)),
+                     ("mixed_fcg", lambda: ctx.solve_fcg(phi_t, 0.0, b, tol=1e-10, a=args.fgmres_a))):
         fn()
         flush.zero_()
         torch.cuda.synchronize()
@@ -314,9 +320,10 @@ def main():
         z.record(stream)
         torch.cuda.synchronize()
         solve[name] = {"ms": a.elapsed_time(z), "iters": info["iters"], "inner_iters": info["iters_inner"],
-                       "true_rel_res": info["true_rel_res"]}
+                       "restarts": info["iters_outer"], "true_rel_res": info["true_rel_res"]}
     solve["speedup_mixed_vs_fp64"] = solve["fp64_cg"]["ms"] / solve["mixed_fgmres"]["ms"]
     solve["workload"] = "102x102x64 lattice, m_s=0, phi of the step, b = rho_0, true residual 1e-10"
+    solve["fgmres_a"] = args.fgmres_a
 
     # the batched workload: 48 uneven lattices x 3 masses = 144 systems at 1e-10,
     # batched mixed vs batched FP64 vs FP64 CG one system at a time
@@ -362,7 +369,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write, untimed)",
+                "config": {"workload": WORKLOAD + "; " + WORKLOAD_A.format(a=args.fgmres_a),
+                           "l2": "flushed between steps (256 MB write, untimed)",
                            "sites": N, "mmdag_applies_per_step": applies / args.steps,
                            "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall},
                 "roofline": roofline, "cpu_baseline": cpu,

@@ -48,19 +48,20 @@ def correlator(ctx, lat, phi, orbital: np.ndarray, t0s: Sequence[int], tol: floa
     n, m, nt = lat.n, lat.m, lat.nt
     N = lat.nsites
     o = torch.tensor(orbital, device="cuda")
-    out = np.zeros(nt, complex)
+    out = torch.zeros(nt, dtype=torch.complex128, device="cuda")
     ctx.load_field(phi)
-    idx_all = [torch.tensor(slice_indices(n, m, nt, t), device="cuda") for t in range(nt)]
+    idx = torch.tensor(np.stack([slice_indices(n, m, nt, t) for t in range(nt)]), device="cuda")  # (nt, 2V)
     for t0 in t0s:
         b = torch.zeros(N, dtype=torch.complex128, device="cuda")
-        b[idx_all[t0]] = o
+        b[idx[t0]] = o
         y, _ = ctx.solve_cg(None, 0.0, b, tol=tol)
         col = ctx.apply_Mdag(None, 0.0, y)
-        for tau in range(nt):
-            t = (t0 + tau) % nt
-            sign = -1.0 if t0 + tau >= nt else 1.0
-            out[tau] += sign * complex(torch.vdot(o, col[idx_all[t]]).item())
-    return out / len(t0s)
+        per_t = col[idx] @ o.conj()                 # projection on every slice t
+        tau = torch.arange(nt, device="cuda")
+        t = (t0 + tau) % nt
+        sign = torch.where(t0 + tau >= nt, -1.0, 1.0).to(torch.complex128)
+        out += sign * per_t[t]
+    return (out / len(t0s)).cpu().numpy()
 
 
 def fit_energy(C: np.ndarray, delta: float, window: Tuple[float, float]) -> float:

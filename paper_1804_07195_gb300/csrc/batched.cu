@@ -73,6 +73,51 @@ __device__ __forceinline__ bool group_sum(double (&v)[K], double* partials, int 
   return true;
 }
 
+// Block total of per-thread partial sums, valid in thread 0: FP32 sums use the
+// float-float reduction (no FP64 instruction per thread), FP64 sums the
+// double shuffle reduction.
+__device__ __forceinline__ double block_total(float v) {
+  float2 t = ff_block_sum(make_float2(v, 0.f));
+  return (double)t.x + (double)t.y;
+}
+__device__ __forceinline__ double block_total(double v) {
+  __shared__ double sm[32];
+  double a[1] = {v};
+  block_sum<1>(a, sm);
+  return a[0];
+}
+
+// Second half of group_sum: thread 0 holds the block total; the last block of
+// the system's group sums the partials (in FP64, that block only).
+__device__ __forceinline__ bool group_finish(double blocktot, double* partials, int base, int count,
+                                             unsigned* ticket, double* tot) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = blocktot;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == (unsigned)count - 1u);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  __shared__ double sm[32];
+  double w[1] = {0.0};
+  for (int b = threadIdx.x; b < count; b += blockDim.x) w[0] += __ldcg(&partials[base + b]);
+  block_sum<1>(w, sm);
+  if (threadIdx.x == 0) {
+    *tot = w[0];
+    *ticket = 0u;
+  }
+  return true;
+}
+
+// Scalars of a system in the compute precision, formed once per block.
+template <typename R>
+struct BScal {
+  R dm, sigma, coef;
+};
+
 #define BLOCK_SYS()                                  \
   __shared__ BSys S_;                                \
   const int s_ = bsys[blockIdx.x];                   \
@@ -146,31 +191,39 @@ __global__ void __launch_bounds__(512) kb_cg_mdag(const BSys* __restrict__ sys, 
                                                   V2<R>* __restrict__ u, double* partials, unsigned* tickets,
                                                   unsigned* ndone) {
   BLOCK_SYS();
-  if (bst[s_].cg.done) return;
+  __shared__ BScal<R> sc;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    skip = bst[s_].cg.done;
+    sc.dm = (R)S_.dm;
+    sc.sigma = (R)S_.sigma;
+  }
+  __syncthreads();
+  if (skip) return;
   const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
-  const R dm = (R)S_.dm, sigma = (R)S_.sigma;
+  const R dm = sc.dm, sigma = sc.sigma;
   const V2<R>* ps = p + S_.off;
   V2<R>* us = u + S_.off;
-  double acc[1] = {0.0};
+  R loc = 0;
   for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
     Nbr nb = neighbours(g, q);
     PairOut<R> o = mdag_pair<R>(g, ph, dm, ps, nb);
     st(us, q, o.a);
     st(us, g.H + q, o.b);
-    R loc = norm2(o.a) + norm2(o.b);
+    loc += norm2(o.a) + norm2(o.b);
     if (sigma != (R)0) loc += sigma * (norm2(ld<R>(ps, q)) + norm2(ld<R>(ps, g.H + q)));
-    acc[0] += (double)loc;
   }
-  double tot[1];
-  if (group_sum<1>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+  const double bt = block_total(loc);
+  double tot;
+  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot) && threadIdx.x == 0) {
     CGScal& c = bst[s_].cg;
-    c.pAp = tot[0];
-    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+    c.pAp = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
       c.alpha = 0.0;
       c.done = CG_BREAKDOWN;
       atomicAdd(ndone, 1u);
     } else {
-      c.alpha = c.rr / tot[0];
+      c.alpha = c.rr / tot;
     }
   }
 }
@@ -183,15 +236,23 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
                                                V2<R>* __restrict__ r, double* partials, unsigned* tickets,
                                                unsigned* ndone) {
   BLOCK_SYS();
-  if (bst[s_].cg.done) return;
+  __shared__ BScal<R> sc;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    skip = bst[s_].cg.done;
+    sc.dm = (R)S_.dm;
+    sc.sigma = (R)S_.sigma;
+    sc.coef = (R)bst[s_].cg.alpha;
+  }
+  __syncthreads();
+  if (skip) return;
   const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
-  const R dm = (R)S_.dm, sigma = (R)S_.sigma, alpha = (R)bst[s_].cg.alpha;
+  const R dm = sc.dm, sigma = sc.sigma, alpha = sc.coef;
   const V2<R>* us = u + S_.off;
-  double acc[1] = {0.0};
+  R loc = 0;
   for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
     Nbr nb = neighbours(g, q);
     PairOut<R> o = m_pair<R>(g, ph, dm, us, nb);
-    R loc = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const long long k = S_.off + (h ? g.H + q : q);
@@ -207,12 +268,12 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
       st(r, k, rk);
       loc += norm2(rk);
     }
-    acc[0] += (double)loc;
   }
-  double tot[1];
-  if (group_sum<1>(acc, partials, S_.block0, S_.nblocks, tickets + s_, tot) && threadIdx.x == 0) {
+  const double bt = block_total(loc);
+  double tot;
+  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot) && threadIdx.x == 0) {
     CGScal& c = bst[s_].cg;
-    const double rr = tot[0];
+    const double rr = tot;
     c.beta = rr / c.rr;
     c.rr = rr;
     c.iter += 1;
@@ -231,8 +292,15 @@ __global__ void __launch_bounds__(512) kb_cg_p(const BSys* __restrict__ sys, con
                                                const BState* bst, const V2<R>* __restrict__ r,
                                                V2<R>* __restrict__ p) {
   BLOCK_SYS();
-  if (bst[s_].cg.done) return;
-  const R beta = (R)bst[s_].cg.beta;
+  __shared__ R sbeta;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    skip = bst[s_].cg.done;
+    sbeta = (R)bst[s_].cg.beta;
+  }
+  __syncthreads();
+  if (skip) return;
+  const R beta = sbeta;
   for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
     const long long i = S_.off + k;
     Cx<R> rk = ld<R>(r, i), pk = ld<R>(p, i);
@@ -573,7 +641,7 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
     HMC_TRY(bmalloc(c, w, (void**)&w.rrbb, sizeof(double) * 2 * nsys));
     HMC_TRY(bmalloc(c, w, (void**)&w.tickets, sizeof(unsigned) * nsys));
     HMC_TRY(bmalloc(c, w, (void**)&w.ndone, sizeof(unsigned)));
-    HMC_TRY(bmalloc(c, w, (void**)&w.partials, sizeof(double) * 2 * max_blocks));
+    HMC_TRY(bmalloc(c, w, (void**)&w.partials, sizeof(double) * 2 * max_blocks));  // K <= 2 values
     HMC_TRY(bmalloc(c, w, (void**)&w.E, sizeof(double2) * Nt));
     HMC_TRY(bmalloc(c, w, (void**)&w.phi32, sizeof(float) * Nt));
     HMC_TRY(bmalloc(c, w, (void**)&w.x, sizeof(double2) * Nt));

@@ -269,6 +269,18 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
                              const hmc_solver_opts* action_opts, double* H0, double* H1,
                              hmc_solve_info* agg);
 
+/* ---- launch shapes ---------------------------------------------------------- */
+
+/* The CG kernels' launch shapes are chosen by an autotuner on a context's first
+ * solve in each precision (timed candidates; see hmc_profile_read for the
+ * choice). For the FP32 CG pair there are two kernel designs: grid-stride
+ * kernels with neighbours read through the caches, and shared-memory tiled
+ * kernels that stage each time slice of a cell tile with its neighbour halo.
+ * variant: 0 = let the autotuner choose among both (default), 1 = grid-stride
+ * only, 2 = tiled only (falls back to grid-stride on lattices too small for a
+ * tile). Setting it re-runs the tuner at the next FP32 solve. */
+hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
+
 /* ---- instrumentation ------------------------------------------------------- */
 
 #define HMC_NKERNELS 32
@@ -280,7 +292,9 @@ typedef struct {
   double bytes_total;   /* algorithmic HBM bytes summed over those launches: each
                            array the kernel must read or write, counted once */
   int threads;          /* launch shape chosen by the autotuner (CG kernels) */
-  int waves;            /* grid = waves x resident blocks (0: one item per thread) */
+  int waves;            /* grid = waves x resident blocks (0: one item per thread);
+                           negative: the tiled FP32 CG kernels with -waves time
+                           slices per tile of `threads` cells */
 } hmc_kernel_stat;
 
 /* Per-kernel launch counters are always kept. With timing on, every launch of

@@ -289,6 +289,10 @@ class Context:
         self._check(self.lib.hmc_solve_batched(self.h, len(systems), arr, 1 if mixed else 0, infos))
         return [i.as_dict() for i in infos]
 
+    def set_cg_variant(self, variant: int):
+        """0: autotune over both FP32 CG kernel designs; 1: grid-stride; 2: tiled."""
+        self._check(self.lib.hmc_set_cg_variant(self.h, variant))
+
     # --- instrumentation ----------------------------------------------------
     def profile(self, timing: bool, reset: bool = True):
         self._check(self.lib.hmc_profile(self.h, 1 if timing else 0, 1 if reset else 0))

@@ -83,7 +83,9 @@ struct GraphEntry {
 struct Shape {
   int threads = 256;
   int waves = 1;
-  int occ = 8;  // resident blocks per SM at this block size
+  int occ = 8;     // resident blocks per SM at this block size
+  int tiled = 0;   // FP32 CG pair: 1 = shared-memory tiled kernels (threads = cells per tile)
+  int tt = 1;      // tiled: time slices per block
 };
 
 struct ProfileState {
@@ -128,6 +130,7 @@ struct hmc_ctx {
   // private non-blocking `cap_stream`, since the legacy stream cannot capture)
   hmc::Shape shape[hmc::K_COUNT];
   bool tuned32 = false, tuned64 = false;
+  int cg32_variant = 0;  // 0 autotune over both designs, 1 grid-stride, 2 tiled
 
   bool use_graphs = true;
   bool capturing = false;
@@ -184,9 +187,16 @@ inline int grid_one(const hmc_ctx* c, long long work) {
   return (int)g;
 }
 
+// Number of float2 reduction partials the FP32 CG buffers partA / partB hold.
+inline long long cg32_part_capacity(const hmc_ctx* c) { return (long long)c->nsm * 2 * kOneItemBlocksPerSM; }
+
 // Grid of a tuned kernel over `work` items.
 inline int shape_grid(const hmc_ctx* c, int id, long long work) {
   const Shape& s = c->shape[id];
+  if (s.tiled) {  // blocks of the tiled FP32 CG kernels (their reduction partials)
+    const Geo& g = c->geo;
+    return ((g.V + s.threads - 1) / s.threads) * ((g.nt + s.tt - 1) / s.tt);
+  }
   long long g = (work + s.threads - 1) / s.threads;
   if (s.waves > 0) {
     const long long cap = (long long)c->nsm * s.occ * s.waves;

@@ -336,6 +336,274 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
   ff_write_partial(loc, partB);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled variants of the FP32 CG pair. A block owns TC consecutive cells
+// [c0, c0 + TC) of the time slices [t0, t0 + TT) and marches through its slices.
+// For every slice it stages, in shared memory, the window of cells
+// (c0 - n - 1 + k) mod V, k < W = TC + 2(n + 1), on both sublattices: that window
+// holds every spatial neighbour of the tile, the wrapped ones included, as long
+// as W <= V (smaller lattices use the grid-stride kernels). Every input element
+// is then read about W / TC times instead of once per neighbour visit, and the
+// time neighbour behind the march comes from a register.
+template <int TC>
+struct TileWin {
+  static constexpr int kMaxN = 256;  // widest lattice the window is sized for
+  float2 a[TC + 2 * (kMaxN + 1)];
+  float2 b[TC + 2 * (kMaxN + 1)];
+};
+
+__device__ __forceinline__ int win_index(int nc, int c0, int n, int V) {
+  int k = nc - (c0 - n - 1);
+  if (k < 0) k += V;
+  if (k >= V) k -= V;
+  return k;
+}
+
+// kernel A, tiled: p_new = r + beta p_old staged per slice; u = M^dagger p_new
+template <int TC>
+__global__ void __launch_bounds__(TC) k_cg32_pmdag_tiled(Geo g, Phase<float> ph, int TT,
+                                                        const float2* __restrict__ r,
+                                                        const float2* __restrict__ pold,
+                                                        float2* __restrict__ pnew,
+                                                        float2* __restrict__ u, CGScal* sc,
+                                                        const float2* __restrict__ partB, int GB,
+                                                        float2* __restrict__ partA) {
+  __shared__ TileWin<TC> win;
+  __shared__ float s_beta, s_dm, s_sigma;
+  __shared__ int s_done;
+  pdl_wait();
+  if (sc->done) return;
+  const int first = sc->first;
+  const double rr_sum = first ? 0.0 : ff_sum_partials(partB, GB);
+  if (threadIdx.x == 0) {
+    const double rr = first ? sc->rr_cur : rr_sum;
+    int done = CG_RUNNING;
+    if (!isfinite(rr))
+      done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      done = CG_MAXIT;
+    const double beta = first ? 0.0 : rr / sc->rr;
+    s_beta = (float)beta;
+    s_dm = (float)sc->dm;
+    s_sigma = (float)sc->sigma;
+    s_done = done;
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      sc->rr_cur = rr;
+      sc->beta = beta;
+      if (done) {
+        sc->rr = rr;
+        sc->done = done;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float dm = s_dm, sigma = s_sigma, beta = s_beta, dk = (float)g.dk;
+  const int n = g.n, V = g.V, H = g.H, nt = g.nt;
+  const int c0 = blockIdx.x * TC;
+  const int c = c0 + threadIdx.x;
+  const bool own = c < V;
+  const int W = TC + 2 * (n + 1);
+  const int t0 = blockIdx.y * TT;
+  const int t1 = min(t0 + TT, nt);
+  // cell coordinates and the window slots of the four spatial partners
+  int kim1 = 0, kjm1 = 0, kip1 = 0, kjp1 = 0, kself = 0;
+  if (own) {
+    const int j = (int)fdiv((uint32_t)c, g.fn);
+    const int i = c - j * n;
+    kself = c - c0 + n + 1;
+    kim1 = win_index(c - 1 + (i == 0 ? n : 0), c0, n, V);
+    kjm1 = win_index(c - n + (j == 0 ? V : 0), c0, n, V);
+    kip1 = win_index(c + 1 - (i == n - 1 ? n : 0), c0, n, V);
+    kjp1 = win_index(c + n - (j == g.m - 1 ? V : 0), c0, n, V);
+  }
+  auto P = [&](int k) {
+    float2 a = r[k], b = pold[k];
+    return Cx<float>{fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y)};
+  };
+  // B at t0 - 1 (the time partner of the B row at t0), carried afterwards
+  Cx<float> pb_prev{0.f, 0.f};
+  if (own) pb_prev = P(H + (t0 == 0 ? (nt - 1) * V : (t0 - 1) * V) + c);
+  float loc = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    const int base = t * V;
+    for (int k = threadIdx.x; k < W; k += TC) {
+      int cell = c0 - n - 1 + k;
+      if (cell < 0) cell += V;
+      if (cell >= V) cell -= V;
+      Cx<float> va = P(base + cell), vb = P(H + base + cell);
+      win.a[k] = make_float2(va.re, va.im);
+      win.b[k] = make_float2(vb.re, vb.im);
+    }
+    __syncthreads();
+    if (own) {
+      const int q = base + c;
+      const bool wrap_tp = (t == nt - 1), wrap_tm = (t == 0);
+      const int qtp = wrap_tp ? c : base + V + c;
+      const int qtm = wrap_tm ? (nt - 1) * V + c : base - V + c;
+      float2 s;
+      s = win.a[kself];
+      Cx<float> pa{s.x, s.y};
+      s = win.b[kself];
+      Cx<float> pb{s.x, s.y};
+      st(pnew, q, pa);
+      st(pnew, H + q, pb);
+      // A row: partner (x, t+1)
+      Cx<float> ea = ph(qtp);
+      Cx<float> za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, wrap_tp);
+      Cx<float> ta = cfma(za, P(qtp), Cx<float>{-pa.re, -pa.im});
+      s = win.b[kim1];
+      Cx<float> b1{s.x, s.y};
+      s = win.b[kjm1];
+      Cx<float> b2{s.x, s.y};
+      Cx<float> oa = hopsum(ta, dk, pb, b1, b2);
+      // B row: partner (x, t-1), carried from the previous slice
+      Cx<float> eb = ph(H + qtm);
+      Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, wrap_tm);
+      Cx<float> tb = cfma(zb, pb_prev, pb);
+      s = win.a[kip1];
+      Cx<float> a1{s.x, s.y};
+      s = win.a[kjp1];
+      Cx<float> a2{s.x, s.y};
+      Cx<float> ob = hopsum(tb, dk, pa, a1, a2);
+      st(u, q, oa);
+      st(u, H + q, ob);
+      loc += norm2(oa) + norm2(ob);
+      if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+      pb_prev = pb;
+    }
+    __syncthreads();
+  }
+  pdl_trigger();
+  float2 v = ff_block_sum(make_float2(loc, 0.f));
+  if (threadIdx.x == 0) partA[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+// kernel B, tiled: u staged per slice; A p = M u + sigma p; x, r updates
+template <int TC>
+__global__ void __launch_bounds__(TC) k_cg32_m_tiled(Geo g, Phase<float> ph, int TT,
+                                                    const float2* __restrict__ u,
+                                                    const float2* __restrict__ p,
+                                                    float2* __restrict__ x, float2* __restrict__ r,
+                                                    CGScal* sc, const float2* __restrict__ partA, int GA,
+                                                    float2* __restrict__ partB) {
+  __shared__ TileWin<TC> win;
+  __shared__ float s_alpha, s_dm, s_sigma;
+  __shared__ int s_bad;
+  pdl_wait();
+  if (sc->done) return;
+  const double pAp = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) {
+    const double rr = sc->rr_cur;
+    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+    s_bad = bad;
+    s_alpha = bad ? 0.f : (float)(rr / pAp);
+    s_dm = (float)sc->dm;
+    s_sigma = (float)sc->sigma;
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      sc->pAp = pAp;
+      sc->rr = rr;
+      sc->first = 0;
+      if (bad) {
+        sc->alpha = 0.0;
+        sc->done = CG_BREAKDOWN;
+      } else {
+        sc->alpha = rr / pAp;
+        sc->iter += 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float dm = s_dm, sigma = s_sigma, alpha = s_alpha, dk = (float)g.dk;
+  const int n = g.n, V = g.V, H = g.H, nt = g.nt;
+  const int c0 = blockIdx.x * TC;
+  const int c = c0 + threadIdx.x;
+  const bool own = c < V;
+  const int W = TC + 2 * (n + 1);
+  const int t0 = blockIdx.y * TT;
+  const int t1 = min(t0 + TT, nt);
+  int kim1 = 0, kjm1 = 0, kip1 = 0, kjp1 = 0, kself = 0;
+  if (own) {
+    const int j = (int)fdiv((uint32_t)c, g.fn);
+    const int i = c - j * n;
+    kself = c - c0 + n + 1;
+    kim1 = win_index(c - 1 + (i == 0 ? n : 0), c0, n, V);
+    kjm1 = win_index(c - n + (j == 0 ? V : 0), c0, n, V);
+    kip1 = win_index(c + 1 - (i == n - 1 ? n : 0), c0, n, V);
+    kjp1 = win_index(c + n - (j == g.m - 1 ? V : 0), c0, n, V);
+  }
+  // A at t0 - 1 (the time partner of the A row at t0), carried afterwards
+  Cx<float> ua_prev{0.f, 0.f};
+  if (own) {
+    float2 v = u[(t0 == 0 ? (nt - 1) * V : (t0 - 1) * V) + c];
+    ua_prev = Cx<float>{v.x, v.y};
+  }
+  float loc = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    const int base = t * V;
+    for (int k = threadIdx.x; k < W; k += TC) {
+      int cell = c0 - n - 1 + k;
+      if (cell < 0) cell += V;
+      if (cell >= V) cell -= V;
+      win.a[k] = u[base + cell];
+      win.b[k] = u[H + base + cell];
+    }
+    __syncthreads();
+    if (own) {
+      const int q = base + c;
+      const bool wrap_tp = (t == nt - 1), wrap_tm = (t == 0);
+      const int qtp = wrap_tp ? c : base + V + c;
+      float2 s;
+      s = win.a[kself];
+      Cx<float> ua{s.x, s.y};
+      s = win.b[kself];
+      Cx<float> ub{s.x, s.y};
+      // A row: (e^{i phi_A(t)} - dm) u_A(t-1)
+      Cx<float> ea = ph(q);
+      Cx<float> za = cneg_if(Cx<float>{ea.re - dm, ea.im}, wrap_tm);
+      Cx<float> ta = cfma(za, ua_prev, Cx<float>{-ua.re, -ua.im});
+      s = win.b[kim1];
+      Cx<float> b1{s.x, s.y};
+      s = win.b[kjm1];
+      Cx<float> b2{s.x, s.y};
+      Cx<float> oa = hopsum(ta, dk, ub, b1, b2);
+      // B row: -(e^{-i phi_B(t)} - dm) u_B(t+1)
+      Cx<float> eb = ph(H + q);
+      Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, eb.im}, wrap_tp);
+      float2 nb = u[H + qtp];
+      Cx<float> tb = cfma(zb, Cx<float>{nb.x, nb.y}, ub);
+      s = win.a[kip1];
+      Cx<float> a1{s.x, s.y};
+      s = win.a[kjp1];
+      Cx<float> a2{s.x, s.y};
+      Cx<float> ob = hopsum(tb, dk, ua, a1, a2);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = h ? H + q : q;
+        Cx<float> Ap = h ? ob : oa;
+        float2 pk = p[k], xk = x[k], rk = r[k];
+        Ap.re = fmaf(sigma, pk.x, Ap.re);
+        Ap.im = fmaf(sigma, pk.y, Ap.im);
+        xk.x = fmaf(alpha, pk.x, xk.x);
+        xk.y = fmaf(alpha, pk.y, xk.y);
+        rk.x = fmaf(-alpha, Ap.re, rk.x);
+        rk.y = fmaf(-alpha, Ap.im, rk.y);
+        x[k] = xk;
+        r[k] = rk;
+        loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
+      }
+      ua_prev = ua;
+    }
+    __syncthreads();
+  }
+  pdl_trigger();
+  float2 v = ff_block_sum(make_float2(loc, 0.f));
+  if (threadIdx.x == 0) partB[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
                                                     const V2<R>* __restrict__ u,
@@ -615,9 +883,9 @@ __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __res
 // captured iteration chunk: the first kernel of a capture (no kernel before it
 // in the graph) and every launch outside a capture are ordinary launches.
 template <typename... KA, typename... A>
-static void launch_pdl(hmc_ctx* c, void (*k)(KA...), int grid, int threads, cudaStream_t s, A... args) {
+static void launch_pdl(hmc_ctx* c, void (*k)(KA...), dim3 grid, int threads, cudaStream_t s, A... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -630,7 +898,7 @@ static void launch_pdl(hmc_ctx* c, void (*k)(KA...), int grid, int threads, cuda
   (void)cudaLaunchKernelEx(&cfg, k, ((KA)args)...);  // errors surface through cudaGetLastError
   if (c->capturing) c->pdl_armed = true;
 }
-#define PDL(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, c->stream
+#define PDL(id, work) dim3(shape_grid(c, (id), (work))), c->shape[(id)].threads, c->stream
 
 // tuned launch shape of a CG kernel
 #define SHAPE(id, work) shape_grid(c, (id), (work)), c->shape[(id)].threads, 0, c->stream
@@ -709,22 +977,56 @@ INST(float)
 INST(double)
 #undef INST
 
+// Tiled variants are usable when the shared-memory window holds the tile's
+// spatial neighbourhood and the grid's reduction partials fit their buffers.
+bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt) {
+  if (g.n > TileWin<256>::kMaxN || tc + 2 * (g.n + 1) > g.V || tt < 1) return false;
+  const long long blocks = (long long)((g.V + tc - 1) / tc) * ((g.nt + tt - 1) / tt);
+  return blocks <= cg32_part_capacity(c);
+}
+
 hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const float2* pold,
                              float2* pnew, float2* u, CGScal* sc, unsigned* ticket) {
   (void)ticket;
   const int GB = shape_grid(c, K_CG_M32, g.H);
+  const Shape& sh = c->shape[K_CG_MDAG32];
+  if (sh.tiled && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    launch_pdl(c, k_cg32_pmdag, PDL(K_CG_MDAG32, g.H), g, phase_of<float>(c), r, pold, pnew, u, sc,
-               (const float2*)c->partB, GB, (float2*)c->partA);
+    if (sh.tiled) {
+      const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
+      const float2* pb = (const float2*)c->partB;
+      float2* pa = (float2*)c->partA;
+      switch (sh.threads) {
+        case 256: launch_pdl(c, k_cg32_pmdag_tiled<256>, grid, 256, c->stream, g, phase_of<float>(c), sh.tt, r, pold, pnew, u, sc, pb, GB, pa); break;
+        case 512: launch_pdl(c, k_cg32_pmdag_tiled<512>, grid, 512, c->stream, g, phase_of<float>(c), sh.tt, r, pold, pnew, u, sc, pb, GB, pa); break;
+        default: launch_pdl(c, k_cg32_pmdag_tiled<1024>, grid, 1024, c->stream, g, phase_of<float>(c), sh.tt, r, pold, pnew, u, sc, pb, GB, pa); break;
+      }
+    } else {
+      launch_pdl(c, k_cg32_pmdag, dim3(shape_grid(c, K_CG_MDAG32, g.H)), sh.threads, c->stream, g,
+                 phase_of<float>(c), r, pold, pnew, u, sc, (const float2*)c->partB, GB, (float2*)c->partA);
+    }
   });
 }
 hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2* p, float2* x,
                          float2* r, CGScal* sc, unsigned* ticket) {
   (void)ticket;
   const int GA = shape_grid(c, K_CG_MDAG32, g.H);
+  const Shape& sh = c->shape[K_CG_M32];
+  if (sh.tiled && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    launch_pdl(c, k_cg32_m, PDL(K_CG_M32, g.H), g, phase_of<float>(c), u, p, x, r, sc,
-               (const float2*)c->partA, GA, (float2*)c->partB);
+    if (sh.tiled) {
+      const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
+      const float2* pa = (const float2*)c->partA;
+      float2* pb = (float2*)c->partB;
+      switch (sh.threads) {
+        case 256: launch_pdl(c, k_cg32_m_tiled<256>, grid, 256, c->stream, g, phase_of<float>(c), sh.tt, u, p, x, r, sc, pa, GA, pb); break;
+        case 512: launch_pdl(c, k_cg32_m_tiled<512>, grid, 512, c->stream, g, phase_of<float>(c), sh.tt, u, p, x, r, sc, pa, GA, pb); break;
+        default: launch_pdl(c, k_cg32_m_tiled<1024>, grid, 1024, c->stream, g, phase_of<float>(c), sh.tt, u, p, x, r, sc, pa, GA, pb); break;
+      }
+    } else {
+      launch_pdl(c, k_cg32_m, dim3(shape_grid(c, K_CG_M32, g.H)), sh.threads, c->stream, g, phase_of<float>(c),
+                 u, p, x, r, sc, (const float2*)c->partA, GA, (float2*)c->partB);
+    }
   });
 }
 

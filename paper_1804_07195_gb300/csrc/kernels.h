@@ -51,6 +51,10 @@ template <typename R>
 hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V2<R>* p, CGScal* sc,
                         double tol2, int maxit, double sigma, unsigned* ticket, double ddm);
 
+// Whether the shared-memory tiled FP32 CG kernels apply to this lattice at
+// `tc` cells and `tt` time slices per tile.
+bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt);
+
 // Resident blocks per SM of a CG kernel at `threads` threads per block.
 int cg_kernel_occupancy(int id, int threads);
 

@@ -83,17 +83,36 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
   cudaEvent_t e0, e1;
   HMC_CUDA(c, cudaEventCreate(&e0));
   HMC_CUDA(c, cudaEventCreate(&e1));
-  const int threads[3] = {128, 256, 512};
-  const int waves[4] = {1, 2, 4, 0};
+  // candidates: {threads, waves, tiled, time slices per tile}
+  std::vector<Shape> cands;
+  const bool want_tiled = sizeof(R) == 4 && c->cg32_variant != 1;
+  if (want_tiled)
+    for (int tc : {256, 512, 1024})
+      for (int tt : {2, 4, 8})
+        if (cg32_tiled_ok(c, g, tc, tt)) {
+          Shape sh;
+          sh.threads = tc;
+          sh.tiled = 1;
+          sh.tt = tt;
+          cands.push_back(sh);
+        }
+  // variant 2 keeps the grid-stride candidates only where no tile fits
+  if (!(sizeof(R) == 4 && c->cg32_variant == 2 && !cands.empty()))
+    for (int th : {128, 256, 512})
+      for (int wv : {1, 2, 4, 0}) {
+        Shape sh;
+        sh.threads = th;
+        sh.waves = wv;
+        cands.push_back(sh);
+      }
   float best = 1e30f;
   Shape keep[3];
-  for (int ti = 0; ti < 3; ++ti) {
-    for (int wi = 0; wi < 4; ++wi) {
+  for (const Shape& cand : cands) {
+    {
       for (int k = 0; k < nk; ++k) {
         Shape& sh = c->shape[ids[k]];
-        sh.threads = threads[ti];
-        sh.waves = waves[wi];
-        sh.occ = cg_kernel_occupancy(ids[k], threads[ti]);
+        sh = cand;
+        sh.occ = cand.tiled ? 1 : cg_kernel_occupancy(ids[k], cand.threads);
       }
       // tolerance 0: no candidate stops early
       HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, 0.0, 1 << 30, sigma, tk, c->delta * ms));

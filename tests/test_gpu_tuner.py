@@ -30,3 +30,30 @@ def test_tuner_end_to_end():
     assert F[(0.2, 1.5)] > F[(0.1, 0.3)]
     assert all(np.isfinite(res.small_force)) and all(np.isfinite(res.large_force))
     assert res.N[0] == res.N[1] >= 1
+
+
+def test_nmd_tuner_on_the_four_site_model(paper):
+    """Algorithm B.1 driving real trajectories (4-site model, nt = 64, where
+    the Omelyan integrator is unstable at N_MD = 8 and stable at 16): the tuned
+    N_MD gives a mean acceptance probability near the 0.66 target."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    from paper_1804_07195_gb300 import chain, nmd_tuner
+    from gpu_util import torch
+    lat = hmc.Lattice(2, 1, 64, 1.0, paper["ed_U_over_kappa"], paper["ed_beta_kappa"])
+    opts = hmc.SolverOpts(method=hmc._abi.HMC_SOLVER_CG64, tol=1e-12)
+
+    def integ(n):
+        return hmc.Integrator(hmc._abi.HMC_INTEG_NESTED_OMELYAN, n, ())
+
+    with hmc.Context(lat) as ctx:
+        ch = chain.Chain(ctx, torch.zeros(lat.nsites, dtype=torch.float64, device="cuda"), [], opts, opts,
+                         seed=661)
+        for _ in range(30):
+            ch.trajectory(integ(24))
+        res = nmd_tuner.tune_nmd(lambda n: chain.acceptance_probability(ch.trajectory(integ(n))[0]),
+                                 nmd0=40, max_total=250)
+        acc = [chain.acceptance_probability(ch.trajectory(integ(res.nmd))[0]) for _ in range(100)]
+    assert res.total_trajectories <= 250
+    assert 8 < res.nmd < 40, res
+    assert 0.4 < float(np.mean(acc)) < 0.92, (res.nmd, np.mean(acc), res.history)

@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -166,7 +167,7 @@ def main():
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -323,6 +324,26 @@ def main():
         torch.cuda.synchronize()
         solve[name] = {"ms": a.elapsed_time(z), "iters": info["iters"], "inner_iters": info["iters_inner"],
                        "restarts": info["iters_outer"], "true_rel_res": info["true_rel_res"]}
+    # the two FP32 CG kernel designs, each pinned in its own context: 300
+    # iterations of single-precision CG (no convergence test reached)
+    designs = {}
+    with hmc.Context(lat) as c2:
+        for vname, v in (("grid_stride", 1), ("tiled", 2)):
+            c2.set_cg_variant(v)
+            b32 = b.to(torch.complex64)
+            c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, info = c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
+            z.record(stream)
+            torch.cuda.synchronize()
+            sh = c2.profile_read()["cg_M_update_f32"]
+            designs[vname] = {"ms": a.elapsed_time(z), "iters": info["iters"],
+                              "us_per_iter": 1e3 * a.elapsed_time(z) / max(info["iters"], 1),
+                              "shape": {"threads": sh["threads"], "waves": sh["waves"]}}
+    solve["fp32_cg_designs"] = designs
     solve["speedup_mixed_vs_fp64"] = solve["fp64_cg"]["ms"] / solve["mixed_fgmres"]["ms"]
     solve["workload"] = "102x102x64 lattice, m_s=0, phi of the step, b = rho_0, true residual 1e-10"
     solve["fgmres_a"] = args.fgmres_a
@@ -330,6 +351,7 @@ def main():
     # the batched workload: 48 uneven lattices x 3 masses = 144 systems at 1e-10,
     # batched mixed vs batched FP64 vs FP64 CG one system at a time
     solve["c4_batched"] = batched_solve_times(hmc, W, torch, stream, flush)
+    solve["apply"] = apply_rates(hmc, W, torch, stream, flush, hbm)
 
     # end to end through the public API with host buffers
     e2e_val = None
@@ -382,6 +404,54 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def apply_rates(hmc, W, torch, stream, flush, hbm):
+    """Operator applications alone: M, M^dagger and M M^dagger in FP32 and FP64
+    on the 102x102x64 lattice (its vectors stay in the 135 MB L2 between
+    applications) and on a 306x306x64 lattice (12M sites, every application
+    streams from HBM). Algorithmic bytes per site of one M or M^dagger: FP32
+    reads the vector (8 B) and phi as float (4 B) and writes 8 B; FP64 reads
+    the vector (16 B) and the phase table e^{i phi} (16 B) and writes 16 B;
+    M M^dagger is the two in sequence."""
+    out = {}
+    per_site = {32: 20.0, 64: 48.0}
+    for name, (n, m, nt) in (("l2_resident_102x102x64", (102, 102, 64)), ("streaming_306x306x64", (306, 306, 64))):
+        lat = hmc.Lattice(n, m, nt, 1.0, 3.8, 12.0)
+        N = lat.nsites
+        g = W.rng(9000 + n)
+        phi = torch.tensor(g.normal(0.0, math.sqrt(lat.delta * 3.8), N), device="cuda")
+        rows = {}
+        with hmc.Context(lat) as ctx:
+            ctx.load_field(phi)
+            for prec in (32, 64):
+                ct = torch.complex64 if prec == 32 else torch.complex128
+                x = torch.randn(N, dtype=ct, device="cuda")
+                for op in ("M", "Mdag", "MMdag"):
+                    fn = {"M": lambda: ctx.apply_M(None, 0.1, x), "Mdag": lambda: ctx.apply_Mdag(None, 0.1, x),
+                          "MMdag": lambda: ctx.apply_MMdag(None, 0.1, x)}[op]
+                    for _ in range(3):
+                        fn()
+                    reps = 20
+                    ts = []
+                    for _ in range(reps):
+                        if name.startswith("streaming"):
+                            flush.zero_()
+                        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        fn()
+                        z.record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(a.elapsed_time(z) * 1e-3)
+                    t = float(np.median(ts))
+                    nbytes = per_site[prec] * N * (2 if op == "MMdag" else 1)
+                    rows[f"{op}_f{prec}"] = {"us": t * 1e6, "gsite_s": N / t / 1e9, "gb_s": nbytes / t / 1e9,
+                                            "frac_hbm": nbytes / t / 1e9 / hbm}
+                del x
+        out[name] = {"sites": N, **rows}
+    out["note"] = ("median of 20 applications timed with CUDA events; the streaming lattice flushes L2 "
+                   "before every application; frac_hbm = algorithmic bytes / time / measured copy peak")
+    return out
 
 
 def batched_solve_times(hmc, W, torch, stream, flush):
@@ -486,7 +556,8 @@ def kernel_case(case):
     phi = torch.tensor(w.phi, device="cuda")
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
-        if case == "spcg":
+        if case in ("spcg", "spcg_grid", "spcg_tiled"):
+            ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2}[case])
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)

@@ -78,7 +78,7 @@ __device__ __forceinline__ bool group_sum(double (&v)[K], double* partials, int 
 // double shuffle reduction.
 __device__ __forceinline__ double block_total(float v) {
   float2 t = ff_block_sum(make_float2(v, 0.f));
-  return (double)t.x + (double)t.y;
+  return threadIdx.x == 0 ? ff_to_double(t) : 0.0;
 }
 __device__ __forceinline__ double block_total(double v) {
   __shared__ double sm[32];

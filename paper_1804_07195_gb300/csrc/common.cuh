@@ -47,7 +47,11 @@ struct Geo {
   int N;   // 2H
   FastDiv fV, fn;
   double dk;  // delta * kappa
+  float dkf;  // the same, rounded once on the host for the FP32 kernels
 };
+
+__device__ __forceinline__ double geo_dk(const Geo& g, double) { return g.dk; }
+__device__ __forceinline__ float geo_dk(const Geo& g, float) { return g.dkf; }
 
 inline Geo make_geo(int n, int m, int nt, double delta, double kappa) {
   Geo g;
@@ -60,6 +64,7 @@ inline Geo make_geo(int n, int m, int nt, double delta, double kappa) {
   g.fV = make_fastdiv((uint32_t)g.V);
   g.fn = make_fastdiv((uint32_t)n);
   g.dk = delta * kappa;
+  g.dkf = (float)g.dk;
   return g;
 }
 
@@ -232,6 +237,7 @@ struct CGScal {
   int iter, maxit;
   int done;      // 0 running, 1 converged, 2 iteration limit, 3 breakdown (pAp <= 0 / NaN)
   int first;     // FP32 pair: no direction yet (beta = 0)
+  float dm32, sigma32;  // dm and sigma rounded once for the FP32 kernels
 };
 
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
@@ -280,11 +286,14 @@ __device__ __forceinline__ void ff_write_partial(float loc, float2* part) {
 
 // Sum of G float-float partials in a fixed order (identical in every block);
 // valid in thread 0 of the calling block, as a double.
-__device__ __forceinline__ double ff_sum_partials(const float2* __restrict__ part, int G) {
+// The pair is returned to every thread; only the thread that forms the
+// block's scalars widens it to double (ff_to_double), so no other thread
+// issues an FP64 instruction.
+__device__ __forceinline__ float2 ff_sum_partials(const float2* __restrict__ part, int G) {
   float2 v = make_float2(0.f, 0.f);
   for (int b = threadIdx.x; b < G; b += blockDim.x) v = ff_add(v, __ldcg(part + b));
-  v = ff_block_sum(v);
-  return (double)v.x + (double)v.y;
+  return ff_block_sum(v);
 }
+__device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
 
 }  // namespace hmc

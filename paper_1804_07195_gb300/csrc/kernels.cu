@@ -202,12 +202,29 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __rest
 //
 // Kernel A (iteration i): rr_i = sum of B's partials; convergence and limit
 // checks; beta = rr_i / rr_{i-1} (0 on the first iteration); then
-//   p_new = r + beta p_old, evaluated at every stencil point it reads (p_old
-//   and p_new are different arrays), u = M^dagger p_new,
+//   p_new = r + beta p_old, u = M^dagger p_new,
 //   partial of pAp = |u|^2 + sigma |p_new|^2.
 // Kernel B: pAp = sum of A's partials, alpha = rr_i / pAp; then
 //   A p = M u + sigma p_new;  x += alpha p_new;  r -= alpha A p;  partial of |r|^2.
 // Block 0 records the scalars in sc for the host.
+//
+// The scalars of a kernel are known only after its block has summed the
+// previous kernel's partials. So that the stencil loads of a thread's first
+// item are in flight during that reduction, each kernel evaluates its first
+// item's stencil before the reduction: kernel B computes M u (which does not
+// depend on alpha), kernel A computes M^dagger r and M^dagger p_old separately
+// and forms M^dagger p_new = M^dagger r + beta M^dagger p_old once beta is
+// known (linearity; both stencils are evaluated afresh from the stored vectors
+// every iteration, so no recurrence error builds up). Later items use the
+// direct form.
+__device__ __forceinline__ void cg32_time_factors(const Phase<float>& ph, const Nbr& nb, int H, float dm,
+                                                  Cx<float>& za, Cx<float>& zb) {
+  Cx<float> ea = ph(nb.tp);
+  za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, nb.wrap_tp);
+  Cx<float> eb = ph(H + nb.tm);
+  zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, nb.wrap_tm);
+}
+
 __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> ph,
                                                          const float2* __restrict__ r,
                                                          const float2* __restrict__ pold,
@@ -215,16 +232,40 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
                                                          float2* __restrict__ u, CGScal* sc,
                                                          const float2* __restrict__ partB, int GB,
                                                          float2* __restrict__ partA) {
-  __shared__ float s_beta, s_dm, s_sigma;
-  __shared__ int s_done;
+  __shared__ float s_beta;
+  __shared__ int s_exit, s_done;
   pdl_wait();
-  if (sc->done) return;
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const int first = sc->first;
+  const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
+  const int H = g.H;
+  const int stride = gridDim.x * blockDim.x;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  // first item: both stencils, before beta is known
+  const bool have0 = q < H;
+  Nbr nb0;
+  PairOut<float> mr{}, mp{};
+  float2 r0a{}, r0b{}, p0a{}, p0b{};
+  if (have0) {
+    nb0 = neighbours(g, q);
+    Cx<float> za, zb;
+    cg32_time_factors(ph, nb0, H, dm, za, zb);
+    mr = mdag_pair_ld<float>(g, za, zb, dk, nb0, [&](int k) { float2 v = r[k]; return Cx<float>{v.x, v.y}; });
+    r0a = r[nb0.q];
+    r0b = r[H + nb0.q];
+    if (!first) {
+      mp = mdag_pair_ld<float>(g, za, zb, dk, nb0, [&](int k) { float2 v = pold[k]; return Cx<float>{v.x, v.y}; });
+      p0a = pold[nb0.q];
+      p0b = pold[H + nb0.q];
+    }
+  }
   // |r|^2: from the init kernel on the first iteration, else from B's partials;
   // the scalars are formed once per block by thread 0
-  const int first = sc->first;
-  const double rr_sum = first ? 0.0 : ff_sum_partials(partB, GB);
+  const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : rr_sum;
+    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
     int done = CG_RUNNING;
     if (!isfinite(rr))
       done = CG_BREAKDOWN;
@@ -234,8 +275,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
       done = CG_MAXIT;
     const double beta = first ? 0.0 : rr / sc->rr;
     s_beta = (float)beta;
-    s_dm = (float)sc->dm;
-    s_sigma = (float)sc->sigma;
     s_done = done;
     if (blockIdx.x == 0) {
       sc->rr_cur = rr;
@@ -248,30 +287,35 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
   }
   __syncthreads();
   if (s_done) return;
-  const float dm = s_dm, sigma = s_sigma, beta = s_beta;
-  const int H = g.H;
-  const float dk = (float)g.dk;
+  const float beta = s_beta;
   float loc = 0.f;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < H; q += gridDim.x * blockDim.x) {
+  if (have0) {
+    Cx<float> pa{fmaf(beta, p0a.x, r0a.x), fmaf(beta, p0a.y, r0a.y)};
+    Cx<float> pb{fmaf(beta, p0b.x, r0b.x), fmaf(beta, p0b.y, r0b.y)};
+    Cx<float> oa{fmaf(beta, mp.a.re, mr.a.re), fmaf(beta, mp.a.im, mr.a.im)};
+    Cx<float> ob{fmaf(beta, mp.b.re, mr.b.re), fmaf(beta, mp.b.im, mr.b.im)};
+    st(pnew, nb0.q, pa);
+    st(pnew, H + nb0.q, pb);
+    st(u, nb0.q, oa);
+    st(u, H + nb0.q, ob);
+    loc += norm2(oa) + norm2(ob);
+    if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+  }
+  for (q += stride; q < H; q += stride) {
     Nbr nb = neighbours(g, q);
     auto P = [&](int k) {
       float2 a = r[k], b = pold[k];
       return Cx<float>{fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y)};
     };
+    Cx<float> za, zb;
+    cg32_time_factors(ph, nb, H, dm, za, zb);
+    PairOut<float> o = mdag_pair_ld<float>(g, za, zb, dk, nb, P);
     Cx<float> pa = P(nb.q), pb = P(H + nb.q);
     st(pnew, nb.q, pa);
     st(pnew, H + nb.q, pb);
-    Cx<float> ea = ph(nb.tp);
-    Cx<float> za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, nb.wrap_tp);
-    Cx<float> ta = cfma(za, P(nb.tp), Cx<float>{-pa.re, -pa.im});
-    Cx<float> oa = hopsum(ta, dk, pb, P(H + nb.im1), P(H + nb.jm1));
-    Cx<float> eb = ph(H + nb.tm);
-    Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, nb.wrap_tm);
-    Cx<float> tb = cfma(zb, P(H + nb.tm), pb);
-    Cx<float> ob = hopsum(tb, dk, pa, P(nb.ip1), P(nb.jp1));
-    st(u, nb.q, oa);
-    st(u, H + nb.q, ob);
-    loc += norm2(oa) + norm2(ob);
+    st(u, nb.q, o.a);
+    st(u, H + nb.q, o.b);
+    loc += norm2(o.a) + norm2(o.b);
     if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
   }
   pdl_trigger();
@@ -284,18 +328,27 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
                                                      float2* __restrict__ x, float2* __restrict__ r,
                                                      CGScal* sc, const float2* __restrict__ partA, int GA,
                                                      float2* __restrict__ partB) {
-  __shared__ float s_alpha, s_dm, s_sigma;
-  __shared__ int s_bad;
+  __shared__ float s_alpha;
+  __shared__ int s_exit, s_bad;
   pdl_wait();
-  if (sc->done) return;
-  const double pAp = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const float dm = sc->dm32, sigma = sc->sigma32;
+  const int H = g.H;
+  const int stride = gridDim.x * blockDim.x;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  // first item: M u before alpha is known
+  const bool have0 = q < H;
+  PairOut<float> o0{};
+  if (have0) o0 = m_pair<float>(g, ph, dm, u, neighbours(g, q));
+  const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
+    const double pAp = ff_to_double(pAp_pair);
     const double rr = sc->rr_cur;
     const bool bad = !(pAp > 0.0) || !isfinite(pAp);
     s_bad = bad;
     s_alpha = bad ? 0.f : (float)(rr / pAp);
-    s_dm = (float)sc->dm;
-    s_sigma = (float)sc->sigma;
     if (blockIdx.x == 0) {
       sc->pAp = pAp;
       sc->rr = rr;
@@ -311,14 +364,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
   }
   __syncthreads();
   if (s_bad) return;
-  const float dm = s_dm, sigma = s_sigma, alpha = s_alpha;
+  const float alpha = s_alpha;
   float loc = 0.f;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.H; q += gridDim.x * blockDim.x) {
-    Nbr nb = neighbours(g, q);
-    PairOut<float> o = m_pair<float>(g, ph, dm, u, nb);
+  auto update = [&](int qq, const PairOut<float>& o) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int k = h ? g.H + q : q;
+      const int k = h ? H + qq : qq;
       Cx<float> Ap = h ? o.b : o.a;
       float2 pk = p[k], xk = x[k], rk = r[k];
       Ap.re = fmaf(sigma, pk.x, Ap.re);
@@ -331,7 +382,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
       r[k] = rk;
       loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
     }
-  }
+  };
+  if (have0) update(q, o0);
+  for (q += stride; q < H; q += stride) update(q, m_pair<float>(g, ph, dm, u, neighbours(g, q)));
   pdl_trigger();
   ff_write_partial(loc, partB);
 }
@@ -369,14 +422,16 @@ __global__ void __launch_bounds__(TC) k_cg32_pmdag_tiled(Geo g, Phase<float> ph,
                                                         const float2* __restrict__ partB, int GB,
                                                         float2* __restrict__ partA) {
   __shared__ TileWin<TC> win;
-  __shared__ float s_beta, s_dm, s_sigma;
-  __shared__ int s_done;
+  __shared__ float s_beta;
+  __shared__ int s_exit, s_done;
   pdl_wait();
-  if (sc->done) return;
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
   const int first = sc->first;
-  const double rr_sum = first ? 0.0 : ff_sum_partials(partB, GB);
+  const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : rr_sum;
+    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
     int done = CG_RUNNING;
     if (!isfinite(rr))
       done = CG_BREAKDOWN;
@@ -386,8 +441,6 @@ __global__ void __launch_bounds__(TC) k_cg32_pmdag_tiled(Geo g, Phase<float> ph,
       done = CG_MAXIT;
     const double beta = first ? 0.0 : rr / sc->rr;
     s_beta = (float)beta;
-    s_dm = (float)sc->dm;
-    s_sigma = (float)sc->sigma;
     s_done = done;
     if (blockIdx.x == 0 && blockIdx.y == 0) {
       sc->rr_cur = rr;
@@ -400,7 +453,7 @@ __global__ void __launch_bounds__(TC) k_cg32_pmdag_tiled(Geo g, Phase<float> ph,
   }
   __syncthreads();
   if (s_done) return;
-  const float dm = s_dm, sigma = s_sigma, beta = s_beta, dk = (float)g.dk;
+  const float dm = sc->dm32, sigma = sc->sigma32, beta = s_beta, dk = g.dkf;
   const int n = g.n, V = g.V, H = g.H, nt = g.nt;
   const int c0 = blockIdx.x * TC;
   const int c = c0 + threadIdx.x;
@@ -490,18 +543,19 @@ __global__ void __launch_bounds__(TC) k_cg32_m_tiled(Geo g, Phase<float> ph, int
                                                     CGScal* sc, const float2* __restrict__ partA, int GA,
                                                     float2* __restrict__ partB) {
   __shared__ TileWin<TC> win;
-  __shared__ float s_alpha, s_dm, s_sigma;
-  __shared__ int s_bad;
+  __shared__ float s_alpha;
+  __shared__ int s_exit, s_bad;
   pdl_wait();
-  if (sc->done) return;
-  const double pAp = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
+    const double pAp = ff_to_double(pAp_pair);
     const double rr = sc->rr_cur;
     const bool bad = !(pAp > 0.0) || !isfinite(pAp);
     s_bad = bad;
     s_alpha = bad ? 0.f : (float)(rr / pAp);
-    s_dm = (float)sc->dm;
-    s_sigma = (float)sc->sigma;
     if (blockIdx.x == 0 && blockIdx.y == 0) {
       sc->pAp = pAp;
       sc->rr = rr;
@@ -517,7 +571,7 @@ __global__ void __launch_bounds__(TC) k_cg32_m_tiled(Geo g, Phase<float> ph, int
   }
   __syncthreads();
   if (s_bad) return;
-  const float dm = s_dm, sigma = s_sigma, alpha = s_alpha, dk = (float)g.dk;
+  const float dm = sc->dm32, sigma = sc->sigma32, alpha = s_alpha, dk = g.dkf;
   const int n = g.n, V = g.V, H = g.H, nt = g.nt;
   const int c0 = blockIdx.x * TC;
   const int c = c0 + threadIdx.x;
@@ -643,6 +697,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
       init->thresh = tol2 * tot[1];
       init->sigma = dsigma;
       init->dm = ddm;
+      init->sigma32 = (float)dsigma;
+      init->dm32 = (float)ddm;
       init->iter = 0;
       init->maxit = maxit;
       init->alpha = init->beta = init->pAp = 0.0;
@@ -675,6 +731,8 @@ __global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restri
     sc->thresh = tol2 * tot[0];
     sc->sigma = sigma;
     sc->dm = ddm;
+    sc->sigma32 = (float)sigma;
+    sc->dm32 = (float)ddm;
     sc->iter = 0;
     sc->maxit = maxit;
     sc->alpha = sc->beta = sc->pAp = 0.0;

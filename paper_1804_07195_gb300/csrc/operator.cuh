@@ -72,7 +72,7 @@ __device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const PH& ph, R dm
                                                 const typename Vec2<R>::type* __restrict__ p,
                                                 const Nbr& nb) {
   const int H = g.H;
-  const R dk = (R)g.dk;
+  const R dk = geo_dk(g, R(0));
   Cx<R> pa = ld<R>(p, nb.q), pb = ld<R>(p, H + nb.q);
   // A row: time partner (x, t+1), phase of A at t+1, conjugated
   Cx<R> ea = ph(nb.tp);
@@ -87,13 +87,28 @@ __device__ __forceinline__ PairOut<R> mdag_pair(const Geo& g, const PH& ph, R dm
   return PairOut<R>{oa, ob};
 }
 
+// M^dagger at the cell-time of nb of the vector returned by the loader L, with
+// the time-hop factors za (A row) and zb (B row) already formed; used where
+// the same stencil is applied to two vectors.
+template <typename R, typename LD>
+__device__ __forceinline__ PairOut<R> mdag_pair_ld(const Geo& g, Cx<R> za, Cx<R> zb, R dk, const Nbr& nb,
+                                                   LD L) {
+  const int H = g.H;
+  Cx<R> pa = L(nb.q), pb = L(H + nb.q);
+  Cx<R> ta = cfma(za, L(nb.tp), Cx<R>{-pa.re, -pa.im});
+  Cx<R> oa = hopsum(ta, dk, pb, L(H + nb.im1), L(H + nb.jm1));
+  Cx<R> tb = cfma(zb, L(H + nb.tm), pb);
+  Cx<R> ob = hopsum(tb, dk, pa, L(nb.ip1), L(nb.jp1));
+  return PairOut<R>{oa, ob};
+}
+
 // M applied at the cell-time of nb, reading u (precision R).
 template <typename R, typename PH = Phase<R>>
 __device__ __forceinline__ PairOut<R> m_pair(const Geo& g, const PH& ph, R dm,
                                              const typename Vec2<R>::type* __restrict__ u,
                                              const Nbr& nb) {
   const int H = g.H;
-  const R dk = (R)g.dk;
+  const R dk = geo_dk(g, R(0));
   Cx<R> ua = ld<R>(u, nb.q), ub = ld<R>(u, H + nb.q);
   // A row: (e^{i phi_A(t)} - dm) u_A(t-1)
   Cx<R> ea = ph(nb.q);

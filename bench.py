@@ -146,10 +146,13 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(tms)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "oracle M M^dagger applications on the 102x102x64 lattice "
-                                   "(bounded sample of the trajectory's operator work)"},
+            "config": {"workload": WORKLOAD + "; " + WORKLOAD_A.format(a=args.fgmres_a),
+                       "sites": 1331712,
+                       "sample": "each step: the oracle's M M^dagger applications on this lattice for "
+                                 "about 4 s (a bounded sample of the trajectory's operator work)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "numpy complex128 oracle M M^dagger on 1,331,712 sites, ~4 s per step"},
+                             "sample": "numpy complex128 oracle M M^dagger on 1,331,712 sites, ~4 s per step, "
+                                       "single-threaded numpy"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -167,7 +170,7 @@ def main():
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "spcg_grid", "spcg_tiled", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -328,7 +331,7 @@ def main():
     # iterations of single-precision CG (no convergence test reached)
     designs = {}
     with hmc.Context(lat) as c2:
-        for vname, v in (("grid_stride", 1), ("tiled", 2)):
+        for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3)):
             c2.set_cg_variant(v)
             b32 = b.to(torch.complex64)
             c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
@@ -409,13 +412,18 @@ def main():
 def apply_rates(hmc, W, torch, stream, flush, hbm):
     """Operator applications alone: M, M^dagger and M M^dagger in FP32 and FP64
     on the 102x102x64 lattice (its vectors stay in the 135 MB L2 between
-    applications) and on a 306x306x64 lattice (12M sites, every application
-    streams from HBM). Algorithmic bytes per site of one M or M^dagger: FP32
-    reads the vector (8 B) and phi as float (4 B) and writes 8 B; FP64 reads
-    the vector (16 B) and the phase table e^{i phi} (16 B) and writes 16 B;
-    M M^dagger is the two in sequence."""
+    applications) and on a 306x306x64 lattice (12M sites, L2 flushed before
+    every application, so each one streams from HBM). Kernel time comes from
+    the library's CUDA events around each launch (no host call overhead).
+    Algorithmic bytes per site of one M or M^dagger: FP32 reads the vector
+    (8 B) and phi as float (4 B) and writes 8 B; FP64 reads the vector (16 B)
+    and the phase table e^{i phi} (16 B) and writes 16 B; M M^dagger is the
+    two in sequence."""
     out = {}
     per_site = {32: 20.0, 64: 48.0}
+    kernels = {("M", 32): ["apply_M_f32"], ("Mdag", 32): ["apply_Mdag_f32"],
+               ("MMdag", 32): ["apply_Mdag_f32", "apply_M_f32"], ("M", 64): ["apply_M_f64"],
+               ("Mdag", 64): ["apply_Mdag_f64"], ("MMdag", 64): ["apply_Mdag_f64", "apply_M_f64"]}
     for name, (n, m, nt) in (("l2_resident_102x102x64", (102, 102, 64)), ("streaming_306x306x64", (306, 306, 64))):
         lat = hmc.Lattice(n, m, nt, 1.0, 3.8, 12.0)
         N = lat.nsites
@@ -432,25 +440,25 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                           "MMdag": lambda: ctx.apply_MMdag(None, 0.1, x)}[op]
                     for _ in range(3):
                         fn()
+                    torch.cuda.synchronize()
                     reps = 20
-                    ts = []
+                    ctx.profile(True, reset=True)
                     for _ in range(reps):
                         if name.startswith("streaming"):
                             flush.zero_()
-                        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a.record(stream)
                         fn()
-                        z.record(stream)
-                        torch.cuda.synchronize()
-                        ts.append(a.elapsed_time(z) * 1e-3)
-                    t = float(np.median(ts))
+                    torch.cuda.synchronize()
+                    prof = ctx.profile_read()
+                    ctx.profile(False, reset=True)
+                    t = sum(prof[k]["ms"] for k in kernels[(op, prec)]) * 1e-3 / reps
                     nbytes = per_site[prec] * N * (2 if op == "MMdag" else 1)
                     rows[f"{op}_f{prec}"] = {"us": t * 1e6, "gsite_s": N / t / 1e9, "gb_s": nbytes / t / 1e9,
                                             "frac_hbm": nbytes / t / 1e9 / hbm}
                 del x
         out[name] = {"sites": N, **rows}
-    out["note"] = ("median of 20 applications timed with CUDA events; the streaming lattice flushes L2 "
-                   "before every application; frac_hbm = algorithmic bytes / time / measured copy peak")
+    out["note"] = ("mean kernel time of 20 applications (CUDA events around each launch inside the library); "
+                   "the streaming lattice flushes L2 before every application; frac_hbm = algorithmic bytes "
+                   "/ time / measured copy peak")
     return out
 
 
@@ -556,8 +564,8 @@ def kernel_case(case):
     phi = torch.tensor(w.phi, device="cuda")
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
-        if case in ("spcg", "spcg_grid", "spcg_tiled"):
-            ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2}[case])
+        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march"):
+            ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3}[case])
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)

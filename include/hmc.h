@@ -273,12 +273,15 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
 
 /* The CG kernels' launch shapes are chosen by an autotuner on a context's first
  * solve in each precision (timed candidates; see hmc_profile_read for the
- * choice). For the FP32 CG pair there are two kernel designs: grid-stride
- * kernels with neighbours read through the caches, and shared-memory tiled
- * kernels that stage each time slice of a cell tile with its neighbour halo.
- * variant: 0 = let the autotuner choose among both (default), 1 = grid-stride
- * only, 2 = tiled only (falls back to grid-stride on lattices too small for a
- * tile). Setting it re-runs the tuner at the next FP32 solve. */
+ * choice). For the FP32 CG pair there are three kernel designs: grid-stride
+ * kernels with neighbours read through the caches; shared-memory tiled
+ * kernels that stage each time slice of a cell tile with its neighbour halo;
+ * and marching kernels in which each thread keeps one cell and walks up in
+ * time, carrying its time neighbours in registers. variant: 0 = let the
+ * autotuner choose among all three (default), 1 = grid-stride only, 2 = tiled
+ * only, 3 = marching only (2 and 3 fall back to grid-stride where their shapes
+ * do not fit the lattice). Setting it re-runs the tuner at the next FP32
+ * solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
 /* ---- instrumentation ------------------------------------------------------- */
@@ -293,8 +296,9 @@ typedef struct {
                            array the kernel must read or write, counted once */
   int threads;          /* launch shape chosen by the autotuner (CG kernels) */
   int waves;            /* grid = waves x resident blocks (0: one item per thread);
-                           negative: the tiled FP32 CG kernels with -waves time
-                           slices per tile of `threads` cells */
+                           -tt: the tiled FP32 CG kernels with tt time slices
+                           per tile of `threads` cells; -(1000 + tt): the
+                           marching kernels, tt slices per block */
 } hmc_kernel_stat;
 
 /* Per-kernel launch counters are always kept. With timing on, every launch of

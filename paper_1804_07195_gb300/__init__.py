@@ -290,7 +290,8 @@ class Context:
         return [i.as_dict() for i in infos]
 
     def set_cg_variant(self, variant: int):
-        """0: autotune over both FP32 CG kernel designs; 1: grid-stride; 2: tiled."""
+        """0: autotune over all FP32 CG kernel designs; 1: grid-stride; 2: tiled;
+        3: marching."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
     # --- instrumentation ----------------------------------------------------

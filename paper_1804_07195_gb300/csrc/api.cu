@@ -425,7 +425,7 @@ hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma,
 
 hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   if (!c) return HMC_ERR_INVALID;
-  if (variant < 0 || variant > 2) return fail(c, HMC_ERR_INVALID, "variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return fail(c, HMC_ERR_INVALID, "variant must be 0, 1, 2 or 3");
   c->cg32_variant = variant;
   c->tuned32 = false;
   destroy_graphs(c);
@@ -457,7 +457,7 @@ hmc_status hmc_profile_read(hmc_ctx* c, hmc_kernel_stat* out, int max, int* coun
     out[n].ms_total = c->prof.ms[i];
     out[n].bytes_total = c->prof.bytes[i];
     out[n].threads = c->shape[i].threads;
-    out[n].waves = c->shape[i].tiled ? -c->shape[i].tt : c->shape[i].waves;
+    out[n].waves = c->shape[i].tiled ? -(c->shape[i].tt + (c->shape[i].tiled == 2 ? 1000 : 0)) : c->shape[i].waves;
     ++n;
   }
   *count = n;

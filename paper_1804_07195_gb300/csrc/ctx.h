@@ -84,8 +84,9 @@ struct Shape {
   int threads = 256;
   int waves = 1;
   int occ = 8;     // resident blocks per SM at this block size
-  int tiled = 0;   // FP32 CG pair: 1 = shared-memory tiled kernels (threads = cells per tile)
-  int tt = 1;      // tiled: time slices per block
+  int tiled = 0;   // FP32 CG pair: 1 = shared-memory tiled kernels, 2 = marching kernels
+                   // (threads = cells per block)
+  int tt = 1;      // tiled or marching: time slices per block
 };
 
 struct ProfileState {
@@ -130,7 +131,7 @@ struct hmc_ctx {
   // private non-blocking `cap_stream`, since the legacy stream cannot capture)
   hmc::Shape shape[hmc::K_COUNT];
   bool tuned32 = false, tuned64 = false;
-  int cg32_variant = 0;  // 0 autotune over both designs, 1 grid-stride, 2 tiled
+  int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching
 
   bool use_graphs = true;
   bool capturing = false;

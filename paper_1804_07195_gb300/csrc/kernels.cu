@@ -658,6 +658,192 @@ __global__ void __launch_bounds__(TC) k_cg32_m_tiled(Geo g, Phase<float> ph, int
   if (threadIdx.x == 0) partB[blockIdx.y * gridDim.x + blockIdx.x] = v;
 }
 
+// ---------------------------------------------------------------------------
+// Marching variants of the FP32 CG pair. A block owns blockDim.x consecutive
+// cells [c0, c0 + blockDim.x) of the time slices [t0, t0 + TT); each thread
+// keeps one cell and walks up in t. The time partners then come from
+// registers (the value one slice ahead is loaded once and becomes the next
+// slice's own value; the one behind is the previous slice's), and the spatial
+// partners at the same slice, which neighbouring threads of the block load,
+// come from L1. No shared memory and no barrier inside the march.
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag_march(Geo g, Phase<float> ph, int TT,
+                                                               const float2* __restrict__ r,
+                                                               const float2* __restrict__ pold,
+                                                               float2* __restrict__ pnew,
+                                                               float2* __restrict__ u, CGScal* sc,
+                                                               const float2* __restrict__ partB, int GB,
+                                                               float2* __restrict__ partA) {
+  __shared__ float s_beta;
+  __shared__ int s_exit, s_done;
+  pdl_wait();
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const int first = sc->first;
+  const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
+  if (threadIdx.x == 0) {
+    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
+    int done = CG_RUNNING;
+    if (!isfinite(rr))
+      done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      done = CG_MAXIT;
+    const double beta = first ? 0.0 : rr / sc->rr;
+    s_beta = (float)beta;
+    s_done = done;
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      sc->rr_cur = rr;
+      sc->beta = beta;
+      if (done) {
+        sc->rr = rr;
+        sc->done = done;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float dm = sc->dm32, sigma = sc->sigma32, beta = s_beta, dk = g.dkf;
+  const int n = g.n, V = g.V, H = g.H, nt = g.nt;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t0 = blockIdx.y * TT;
+  const int t1 = min(t0 + TT, nt);
+  float loc = 0.f;
+  if (c < V) {
+    const int j = (int)fdiv((uint32_t)c, g.fn);
+    const int i = c - j * n;
+    const int cim1 = c - 1 + (i == 0 ? n : 0), cjm1 = c - n + (j == 0 ? V : 0);
+    const int cip1 = c + 1 - (i == n - 1 ? n : 0), cjp1 = c + n - (j == g.m - 1 ? V : 0);
+    auto P = [&](int k) {
+      float2 a = r[k], b = pold[k];
+      return Cx<float>{fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y)};
+    };
+    Cx<float> pb_prev = P(H + (t0 == 0 ? (nt - 1) * V : (t0 - 1) * V) + c);  // B at t0 - 1
+    Cx<float> pa = P(t0 * V + c);                                             // A at t0
+    for (int t = t0; t < t1; ++t) {
+      const int base = t * V, q = base + c;
+      const bool wrap_tp = (t == nt - 1), wrap_tm = (t == 0);
+      const int qtp = wrap_tp ? c : q + V;
+      const int qtm = wrap_tm ? (nt - 1) * V + c : q - V;
+      const Cx<float> pb = P(H + q);
+      const Cx<float> pa_next = P(qtp);
+      // A row: partner (x, t+1)
+      Cx<float> ea = ph(qtp);
+      Cx<float> za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, wrap_tp);
+      Cx<float> ta = cfma(za, pa_next, Cx<float>{-pa.re, -pa.im});
+      Cx<float> oa = hopsum(ta, dk, pb, P(H + base + cim1), P(H + base + cjm1));
+      // B row: partner (x, t-1), carried
+      Cx<float> eb = ph(H + qtm);
+      Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, wrap_tm);
+      Cx<float> tb = cfma(zb, pb_prev, pb);
+      Cx<float> ob = hopsum(tb, dk, pa, P(base + cip1), P(base + cjp1));
+      st(pnew, q, pa);
+      st(pnew, H + q, pb);
+      st(u, q, oa);
+      st(u, H + q, ob);
+      loc += norm2(oa) + norm2(ob);
+      if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+      pb_prev = pb;
+      pa = pa_next;
+    }
+  }
+  pdl_trigger();
+  float2 v = ff_block_sum(make_float2(loc, 0.f));
+  if (threadIdx.x == 0) partA[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_m_march(Geo g, Phase<float> ph, int TT,
+                                                           const float2* __restrict__ u,
+                                                           const float2* __restrict__ p,
+                                                           float2* __restrict__ x, float2* __restrict__ r,
+                                                           CGScal* sc, const float2* __restrict__ partA, int GA,
+                                                           float2* __restrict__ partB) {
+  __shared__ float s_alpha;
+  __shared__ int s_exit, s_bad;
+  pdl_wait();
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const float2 pAp_pair = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) {
+    const double pAp = ff_to_double(pAp_pair);
+    const double rr = sc->rr_cur;
+    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+    s_bad = bad;
+    s_alpha = bad ? 0.f : (float)(rr / pAp);
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      sc->pAp = pAp;
+      sc->rr = rr;
+      sc->first = 0;
+      if (bad) {
+        sc->alpha = 0.0;
+        sc->done = CG_BREAKDOWN;
+      } else {
+        sc->alpha = rr / pAp;
+        sc->iter += 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float dm = sc->dm32, sigma = sc->sigma32, alpha = s_alpha, dk = g.dkf;
+  const int n = g.n, V = g.V, H = g.H, nt = g.nt;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t0 = blockIdx.y * TT;
+  const int t1 = min(t0 + TT, nt);
+  float loc = 0.f;
+  if (c < V) {
+    const int j = (int)fdiv((uint32_t)c, g.fn);
+    const int i = c - j * n;
+    const int cim1 = c - 1 + (i == 0 ? n : 0), cjm1 = c - n + (j == 0 ? V : 0);
+    const int cip1 = c + 1 - (i == n - 1 ? n : 0), cjp1 = c + n - (j == g.m - 1 ? V : 0);
+    auto U = [&](int k) {
+      float2 v = u[k];
+      return Cx<float>{v.x, v.y};
+    };
+    Cx<float> ua_prev = U((t0 == 0 ? (nt - 1) * V : (t0 - 1) * V) + c);  // A at t0 - 1
+    Cx<float> ub = U(H + t0 * V + c);                                    // B at t0
+    for (int t = t0; t < t1; ++t) {
+      const int base = t * V, q = base + c;
+      const bool wrap_tp = (t == nt - 1), wrap_tm = (t == 0);
+      const int qtp = wrap_tp ? c : q + V;
+      const Cx<float> ua = U(q);
+      const Cx<float> ub_next = U(H + qtp);
+      // A row: (e^{i phi_A(t)} - dm) u_A(t-1), carried
+      Cx<float> ea = ph(q);
+      Cx<float> za = cneg_if(Cx<float>{ea.re - dm, ea.im}, wrap_tm);
+      Cx<float> ta = cfma(za, ua_prev, Cx<float>{-ua.re, -ua.im});
+      Cx<float> oa = hopsum(ta, dk, ub, U(H + base + cim1), U(H + base + cjm1));
+      // B row: -(e^{-i phi_B(t)} - dm) u_B(t+1)
+      Cx<float> eb = ph(H + q);
+      Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, eb.im}, wrap_tp);
+      Cx<float> tb = cfma(zb, ub_next, ub);
+      Cx<float> ob = hopsum(tb, dk, ua, U(base + cip1), U(base + cjp1));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = h ? H + q : q;
+        Cx<float> Ap = h ? ob : oa;
+        float2 pk = p[k], xk = x[k], rk = r[k];
+        Ap.re = fmaf(sigma, pk.x, Ap.re);
+        Ap.im = fmaf(sigma, pk.y, Ap.im);
+        xk.x = fmaf(alpha, pk.x, xk.x);
+        xk.y = fmaf(alpha, pk.y, xk.y);
+        rk.x = fmaf(-alpha, Ap.re, rk.x);
+        rk.y = fmaf(-alpha, Ap.im, rk.y);
+        x[k] = xk;
+        r[k] = rk;
+        loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
+      }
+      ua_prev = ua;
+      ub = ub_next;
+    }
+  }
+  pdl_trigger();
+  float2 v = ff_block_sum(make_float2(loc, 0.f));
+  if (threadIdx.x == 0) partB[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
                                                     const V2<R>* __restrict__ u,
@@ -1037,6 +1223,12 @@ INST(double)
 
 // Tiled variants are usable when the shared-memory window holds the tile's
 // spatial neighbourhood and the grid's reduction partials fit their buffers.
+bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt) {
+  if (tt < 1 || threads < 32 || threads > kMaxThreads) return false;
+  const long long blocks = (long long)((g.V + threads - 1) / threads) * ((g.nt + tt - 1) / tt);
+  return blocks <= cg32_part_capacity(c);
+}
+
 bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt) {
   if (g.n > TileWin<256>::kMaxN || tc + 2 * (g.n + 1) > g.V || tt < 1) return false;
   const long long blocks = (long long)((g.V + tc - 1) / tc) * ((g.nt + tt - 1) / tt);
@@ -1048,9 +1240,14 @@ hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const fl
   (void)ticket;
   const int GB = shape_grid(c, K_CG_M32, g.H);
   const Shape& sh = c->shape[K_CG_MDAG32];
-  if (sh.tiled && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
+  if (sh.tiled == 1 && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
+  if (sh.tiled == 2 && !cg32_march_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "CG shape does not fit");
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    if (sh.tiled) {
+    if (sh.tiled == 2) {
+      const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
+      launch_pdl(c, k_cg32_pmdag_march, grid, sh.threads, c->stream, g, phase_of<float>(c), sh.tt, r, pold, pnew,
+                 u, sc, (const float2*)c->partB, GB, (float2*)c->partA);
+    } else if (sh.tiled) {
       const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
       const float2* pb = (const float2*)c->partB;
       float2* pa = (float2*)c->partA;
@@ -1070,9 +1267,14 @@ hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2
   (void)ticket;
   const int GA = shape_grid(c, K_CG_MDAG32, g.H);
   const Shape& sh = c->shape[K_CG_M32];
-  if (sh.tiled && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
+  if (sh.tiled == 1 && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
+  if (sh.tiled == 2 && !cg32_march_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "CG shape does not fit");
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    if (sh.tiled) {
+    if (sh.tiled == 2) {
+      const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
+      launch_pdl(c, k_cg32_m_march, grid, sh.threads, c->stream, g, phase_of<float>(c), sh.tt, u, p, x, r, sc,
+                 (const float2*)c->partA, GA, (float2*)c->partB);
+    } else if (sh.tiled) {
       const dim3 grid((g.V + sh.threads - 1) / sh.threads, (g.nt + sh.tt - 1) / sh.tt);
       const float2* pa = (const float2*)c->partA;
       float2* pb = (float2*)c->partB;

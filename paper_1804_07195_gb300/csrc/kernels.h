@@ -54,6 +54,9 @@ hmc_status init0_launch(hmc_ctx* c, int N, const V2<R>* b, V2<R>* x, V2<R>* r, V
 // Whether the shared-memory tiled FP32 CG kernels apply to this lattice at
 // `tc` cells and `tt` time slices per tile.
 bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt);
+// Whether the marching FP32 CG kernels' reduction partials fit their buffers
+// at `threads` cells and `tt` time slices per block.
+bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt);
 
 // Resident blocks per SM of a CG kernel at `threads` threads per block.
 int cg_kernel_occupancy(int id, int threads);

@@ -86,7 +86,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
   // candidates: {threads, waves, tiled, time slices per tile}
   std::vector<Shape> cands;
   const bool want_tiled = sizeof(R) == 4 && c->cg32_variant != 1;
-  if (want_tiled)
+  if (want_tiled && c->cg32_variant != 3)
     for (int tc : {256, 512, 1024})
       for (int tt : {2, 4, 8})
         if (cg32_tiled_ok(c, g, tc, tt)) {
@@ -96,8 +96,18 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           sh.tt = tt;
           cands.push_back(sh);
         }
-  // variant 2 keeps the grid-stride candidates only where no tile fits
-  if (!(sizeof(R) == 4 && c->cg32_variant == 2 && !cands.empty()))
+  if (want_tiled && c->cg32_variant != 2)
+    for (int th : {128, 256, 512})
+      for (int tt : {2, 4, 8})
+        if (cg32_march_ok(c, g, th, tt)) {
+          Shape sh;
+          sh.threads = th;
+          sh.tiled = 2;
+          sh.tt = tt;
+          cands.push_back(sh);
+        }
+  // variants 2 and 3 keep the grid-stride candidates only where none of theirs fits
+  if (!(sizeof(R) == 4 && c->cg32_variant >= 2 && !cands.empty()))
     for (int th : {128, 256, 512})
       for (int wv : {1, 2, 4, 0}) {
         Shape sh;

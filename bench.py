@@ -170,7 +170,7 @@ def main():
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -291,8 +291,8 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
-        if tj.get("kernel") == dname and tj.get("source_sha") == kernel_source_sha():
-            traffic = tj["bytes_per_launch"]
+        if tj.get("source_sha") == kernel_source_sha() and dname in tj.get("kernels", {}):
+            traffic = tj["kernels"][dname]
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -331,7 +331,7 @@ def main():
     # iterations of single-precision CG (no convergence test reached)
     designs = {}
     with hmc.Context(lat) as c2:
-        for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3)):
+        for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3), ("persistent", 4)):
             c2.set_cg_variant(v)
             b32 = b.to(torch.complex64)
             c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
@@ -564,8 +564,9 @@ def kernel_case(case):
     phi = torch.tensor(w.phi, device="cuda")
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
-        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march"):
-            ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3}[case])
+        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist"):
+            ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
+                                "spcg_persist": 4}[case])
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)

@@ -273,15 +273,18 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
 
 /* The CG kernels' launch shapes are chosen by an autotuner on a context's first
  * solve in each precision (timed candidates; see hmc_profile_read for the
- * choice). For the FP32 CG pair there are three kernel designs: grid-stride
- * kernels with neighbours read through the caches; shared-memory tiled
- * kernels that stage each time slice of a cell tile with its neighbour halo;
- * and marching kernels in which each thread keeps one cell and walks up in
- * time, carrying its time neighbours in registers. variant: 0 = let the
- * autotuner choose among all three (default), 1 = grid-stride only, 2 = tiled
- * only, 3 = marching only (2 and 3 fall back to grid-stride where their shapes
- * do not fit the lattice). Setting it re-runs the tuner at the next FP32
- * solve. */
+ * choice). FP32 CG has four kernel designs: three two-kernel-per-iteration
+ * pairs — grid-stride kernels with neighbours read through the caches;
+ * shared-memory tiled kernels that stage each time slice of a cell tile with
+ * its neighbour halo; marching kernels in which each thread keeps one cell
+ * and walks up in time, carrying its time neighbours in registers — and a
+ * persistent kernel that runs the whole solve in one cooperative launch with
+ * grid barriers (bounded waits; a wait that gives up returns
+ * HMC_ERR_TIMEOUT) and keeps x and its own entries of r and p in shared
+ * memory. variant: 0 = let the autotuner choose among all four (default),
+ * 1 = grid-stride only, 2 = tiled only, 3 = marching only, 4 = persistent
+ * (2 to 4 fall back to grid-stride where they do not fit the lattice).
+ * Setting it re-runs the tuner at the next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
 /* ---- instrumentation ------------------------------------------------------- */

@@ -291,7 +291,7 @@ class Context:
 
     def set_cg_variant(self, variant: int):
         """0: autotune over all FP32 CG kernel designs; 1: grid-stride; 2: tiled;
-        3: marching."""
+        3: marching; 4: persistent (one cooperative launch per solve)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
     # --- instrumentation ----------------------------------------------------

@@ -240,6 +240,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   if ((e = cudaMalloc(&c->tickets, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->gbar, sizeof(GridBar))) != cudaSuccess) return bail(e);
+  if ((e = cudaMemset(c->gbar, 0, sizeof(GridBar))) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->sc, 0, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
   // one-item grids of the tuned kernels may reach nsm * 128 blocks of 128 threads
   if ((e = cudaFree(c->partials)) != cudaSuccess) return bail(e);
@@ -264,6 +266,7 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   if (c->partB) cudaFree(c->partB);
   if (c->tickets) cudaFree(c->tickets);
   if (c->sc) cudaFree(c->sc);
+  if (c->gbar) cudaFree(c->gbar);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->dscal) cudaFree(c->dscal);
   if (c->dscal_host) cudaFreeHost(c->dscal_host);
@@ -425,9 +428,10 @@ hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma,
 
 hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   if (!c) return HMC_ERR_INVALID;
-  if (variant < 0 || variant > 3) return fail(c, HMC_ERR_INVALID, "variant must be 0, 1, 2 or 3");
+  if (variant < 0 || variant > 4) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 4");
   c->cg32_variant = variant;
   c->tuned32 = false;
+  c->persist32 = false;
   destroy_graphs(c);
   return HMC_OK;
 }

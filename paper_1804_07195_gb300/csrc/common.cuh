@@ -240,7 +240,17 @@ struct CGScal {
   float dm32, sigma32;  // dm and sigma rounded once for the FP32 kernels
 };
 
-enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_TIMEOUT = 4 };
+
+// State of a grid-wide barrier between the co-resident blocks of a cooperative
+// launch: arrivals counted in `count`, release by advancing `gen`; `err` is
+// set when a wait gave up (every later barrier then returns at once).
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
 
 // ---------------------------------------------------------------------------
 // Float-float sums for the FP32 kernels. GB300 executes FP64 at 1/58 of the FP32

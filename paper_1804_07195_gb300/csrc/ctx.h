@@ -43,6 +43,7 @@ enum KernelId {
   K_BATCH_INIT,
   K_BATCH_RESID,
   K_BATCH_MISC,
+  K_CG_PERSIST32,
   K_COUNT
 };
 
@@ -120,6 +121,7 @@ struct hmc_ctx {
   double* partB = nullptr;         // per-block partials of the FP32 CG M kernel
   unsigned int* tickets = nullptr; // one ticket per concurrent reduction site
   hmc::CGScal* sc = nullptr;       // device CG state (two: FP64 outer, FP32 inner)
+  hmc::GridBar* gbar = nullptr;    // grid barrier of the persistent FP32 CG kernel
   hmc::CGScal* sc_host = nullptr;  // pinned mirror
   double* dscal = nullptr;         // device scalar results (64 doubles)
   double* dscal_host = nullptr;    // pinned mirror
@@ -131,7 +133,9 @@ struct hmc_ctx {
   // private non-blocking `cap_stream`, since the legacy stream cannot capture)
   hmc::Shape shape[hmc::K_COUNT];
   bool tuned32 = false, tuned64 = false;
-  int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching
+  int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching,
+                         // 4 persistent
+  bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
 
   bool use_graphs = true;
   bool capturing = false;

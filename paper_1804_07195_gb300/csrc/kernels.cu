@@ -13,7 +13,7 @@ const char* const kKernelNames[K_COUNT] = {
     "cg_p_f32",       "residual_f64",   "residual_f32",  "cg_init0",       "convert",
     "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
     "force",          "axpy",           "md_update",     "batch_cg_graph_f64", "batch_cg_graph_f32",
-    "batch_init",     "batch_residual", "batch_misc"};
+    "batch_init",     "batch_residual", "batch_misc",   "cg_persist_f32"};
 
 const double kKernelBytesPerSite[K_COUNT] = {
     8 + 16 + 4,          // phase: phi in, E and phi32 out
@@ -39,7 +39,8 @@ const double kKernelBytesPerSite[K_COUNT] = {
     16 + 16 + 16 + 16 + 16,  // force: eta, E, xi, chi, grad rw
     24,                  // axpy
     24,                  // md update
-    192, 96, 16 * 4, 16 * 5, 0};
+    192, 96, 16 * 4, 16 * 5, 0,
+    0};  // persistent CG: 56 B per site and iteration, counted after the solve
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restrict__ phi,
@@ -842,6 +843,283 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m_march(Geo g, Phase<float
   pdl_trigger();
   float2 v = ff_block_sum(make_float2(loc, 0.f));
   if (threadIdx.x == 0) partB[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent FP32 CG: the whole solve in one cooperative launch. Every block
+// is resident for the duration and owns the cell-times [q0, q0 + ipb); it
+// keeps x, and its own entries of r and p, in shared memory across
+// iterations, so x never travels to memory until the end and the updates of
+// the second half-iteration read no vector but u. An iteration is the same CG
+// step as the two-kernel pair (p = r + beta p, u = M^dagger p, pAp, alpha,
+// A p = M u + sigma p, x and r updates, |r|^2), with the kernel boundaries
+// replaced by grid barriers and the block partials summed by every block in
+// the same fixed order. The barrier waits are bounded: a wait that gives up
+// marks the solve CG_TIMEOUT and every block leaves.
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    volatile int* verr = &gb->err;
+    int ok = (*verr == 0);
+    if (ok) {
+      const unsigned my = *vgen;
+      __threadfence();
+      if (atomicAdd(&gb->count, 1u) == nblocks - 1u) {
+        atomicExch(&gb->count, 0u);
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*vgen == my) {
+          if (*verr) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > limit) {
+            atomicExch(&gb->err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr int kPersistThreads = 256;
+
+__global__ void __launch_bounds__(kPersistThreads, 4)
+    k_cg32_persist(Geo g, Phase<float> ph, float2* __restrict__ x, float2* __restrict__ r,
+                   float2* __restrict__ p0, float2* __restrict__ p1, float2* __restrict__ u, CGScal* sc,
+                   float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
+                   int ipb) {
+  extern __shared__ float4 s_state[];
+  float4* sx = s_state;         // x at the block's cell-times: (A.re, A.im, B.re, B.im)
+  float4* sp = s_state + ipb;   // p
+  float4* sr = sp + ipb;        // r
+  __shared__ float s_a;
+  __shared__ int s_stop;
+  const int H = g.H;
+  const int q0 = blockIdx.x * ipb;
+  const int nloc = max(0, min(ipb, H - q0));
+  for (int k = threadIdx.x; k < nloc; k += blockDim.x) {
+    const int q = q0 + k;
+    const float2 xa = x[q], xb = x[H + q], pa = p0[q], pb = p0[H + q], ra = r[q], rb = r[H + q];
+    sx[k] = make_float4(xa.x, xa.y, xb.x, xb.y);
+    sp[k] = make_float4(pa.x, pa.y, pb.x, pb.y);
+    sr[k] = make_float4(ra.x, ra.y, rb.x, rb.y);
+  }
+  const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
+  // scalars, held by thread 0 in FP64 and handed to the block as floats
+  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  int iter = sc->iter, done = sc->done;
+  const int maxit = sc->maxit;
+  const double thresh = sc->thresh;
+  float2* pold = p0;
+  float2* pnew = p1;
+  bool first = true;
+  __syncthreads();
+  for (;;) {
+    // convergence and limit checks (the same decision in every block)
+    if (threadIdx.x == 0) {
+      if (!done) {
+        if (!isfinite(rr))
+          done = CG_BREAKDOWN;
+        else if (rr <= thresh)
+          done = CG_CONVERGED;
+        else if (iter >= maxit)
+          done = CG_MAXIT;
+      }
+      beta = first ? 0.0 : rr / rr_prev;
+      s_a = (float)beta;
+      s_stop = done;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const float fb = s_a;
+    // first half: p = r + beta p, u = M^dagger p, partial of |u|^2 + sigma |p|^2
+    float loc = 0.f;
+    for (int k = threadIdx.x; k < nloc; k += blockDim.x) {
+      const int q = q0 + k;
+      const Nbr nb = neighbours(g, q);
+      const float4 ro = sr[k], po = sp[k];
+      const Cx<float> pa{fmaf(fb, po.x, ro.x), fmaf(fb, po.y, ro.y)};
+      const Cx<float> pb{fmaf(fb, po.z, ro.z), fmaf(fb, po.w, ro.w)};
+      // r and p were written by other blocks during this launch: loads skip
+      // L1 (not coherent across SMs) and read L2
+      auto P = [&](int kk) {
+        const float2 a = __ldcg(r + kk), bb = __ldcg(pold + kk);
+        return Cx<float>{fmaf(fb, bb.x, a.x), fmaf(fb, bb.y, a.y)};
+      };
+      Cx<float> ea = ph(nb.tp);
+      Cx<float> za = cneg_if(Cx<float>{ea.re - dm, -ea.im}, nb.wrap_tp);
+      Cx<float> ta = cfma(za, P(nb.tp), Cx<float>{-pa.re, -pa.im});
+      Cx<float> oa = hopsum(ta, dk, pb, P(H + nb.im1), P(H + nb.jm1));
+      Cx<float> eb = ph(H + nb.tm);
+      Cx<float> zb = cneg_if(Cx<float>{dm - eb.re, -eb.im}, nb.wrap_tm);
+      Cx<float> tb = cfma(zb, P(H + nb.tm), pb);
+      Cx<float> ob = hopsum(tb, dk, pa, P(nb.ip1), P(nb.jp1));
+      sp[k] = make_float4(pa.re, pa.im, pb.re, pb.im);
+      st(pnew, q, pa);
+      st(pnew, H + q, pb);
+      st(u, q, oa);
+      st(u, H + q, ob);
+      loc += norm2(oa) + norm2(ob);
+      if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partA[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, gridDim.x, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    {
+      const float2 tot = ff_sum_partials(partA, gridDim.x);
+      if (threadIdx.x == 0) {
+        pAp = ff_to_double(tot);
+        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+        alpha = bad ? 0.0 : rr / pAp;
+        if (bad) done = CG_BREAKDOWN;
+        s_a = (float)alpha;
+        s_stop = bad;
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    const float fa = s_a;
+    // second half: A p = M u + sigma p, x += alpha p, r -= alpha A p, partial of |r|^2
+    loc = 0.f;
+    for (int k = threadIdx.x; k < nloc; k += blockDim.x) {
+      const int q = q0 + k;
+      const PairOut<float> o = m_pair_ld<float>(g, ph, dm, neighbours(g, q), [&](int kk) {
+        const float2 v = __ldcg(u + kk);
+        return Cx<float>{v.x, v.y};
+      });
+      const float4 po = sp[k];
+      float4 xo = sx[k], ro = sr[k];
+      const float apar = fmaf(sigma, po.x, o.a.re), apai = fmaf(sigma, po.y, o.a.im);
+      const float apbr = fmaf(sigma, po.z, o.b.re), apbi = fmaf(sigma, po.w, o.b.im);
+      xo.x = fmaf(fa, po.x, xo.x);
+      xo.y = fmaf(fa, po.y, xo.y);
+      xo.z = fmaf(fa, po.z, xo.z);
+      xo.w = fmaf(fa, po.w, xo.w);
+      ro.x = fmaf(-fa, apar, ro.x);
+      ro.y = fmaf(-fa, apai, ro.y);
+      ro.z = fmaf(-fa, apbr, ro.z);
+      ro.w = fmaf(-fa, apbi, ro.w);
+      sx[k] = xo;
+      sr[k] = ro;
+      r[q] = make_float2(ro.x, ro.y);
+      r[H + q] = make_float2(ro.z, ro.w);
+      loc = fmaf(ro.x, ro.x, fmaf(ro.y, ro.y, fmaf(ro.z, ro.z, fmaf(ro.w, ro.w, loc))));
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partB[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, gridDim.x, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    {
+      const float2 tot = ff_sum_partials(partB, gridDim.x);
+      if (threadIdx.x == 0) {
+        rr_prev = rr;
+        rr = ff_to_double(tot);
+        ++iter;
+      }
+    }
+    first = false;
+    float2* t = pold;
+    pold = pnew;
+    pnew = t;
+  }
+  // x back to memory; block 0 records the state for the host
+  for (int k = threadIdx.x; k < nloc; k += blockDim.x) {
+    const int q = q0 + k;
+    const float4 xo = sx[k];
+    x[q] = make_float2(xo.x, xo.y);
+    x[H + q] = make_float2(xo.z, xo.w);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rr = rr;
+    sc->rr_cur = rr;
+    sc->pAp = pAp;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->iter = iter;
+    sc->first = 0;
+    sc->done = done ? done : CG_MAXIT;
+  }
+}
+
+// Launch plan of the persistent kernel: 4, 3, 2 or 1 resident blocks of
+// kPersistThreads per SM, each with the 48 bytes of shared state of ipb
+// cell-times; false when the lattice's state does not fit on chip.
+static bool persist_plan(const hmc_ctx* c, const Geo& g, int* blocks, int* ipb, size_t* smem) {
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  for (int per_sm = 4; per_sm >= 1; --per_sm) {
+    const int nb = per_sm * c->nsm;
+    const int ib = (g.H + nb - 1) / nb;
+    const size_t sm = (size_t)ib * 3 * sizeof(float4);
+    if ((long long)nb > cg32_part_capacity(c) || sm > (size_t)dev_smem) continue;
+    if (cudaFuncSetAttribute((const void*)k_cg32_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg32_persist, kPersistThreads, sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (occ < per_sm) continue;
+    *blocks = nb;
+    *ipb = ib;
+    *smem = sm;
+    return true;
+  }
+  return false;
+}
+
+bool cg32_persist_ok(const hmc_ctx* c, const Geo& g) {
+  int b, i;
+  size_t s;
+  return persist_plan(c, g, &b, &i, &s);
+}
+
+hmc_status cg32_persist_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1,
+                               float2* u, CGScal* sc) {
+  int blocks = 0, ipb = 0;
+  size_t smem = 0;
+  if (!persist_plan(c, g, &blocks, &ipb, &smem))
+    return fail(c, HMC_ERR_INVALID, "persistent CG state does not fit on chip");
+  HMC_CUDA(c, cudaMemsetAsync(c->gbar, 0, sizeof(GridBar), c->stream));
+  Phase<float> ph = phase_of<float>(c);
+  float2* pa = (float2*)c->partA;
+  float2* pb = (float2*)c->partB;
+  GridBar* gb = c->gbar;
+  // about one second of SM clock per barrier wait before giving up
+  long long limit = 2000000000LL;
+  Geo gg = g;
+  void* args[] = {&gg, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &ipb};
+  cudaError_t le = cudaSuccess;
+  HMC_TRY(launch_b(c, K_CG_PERSIST32, 0.0, [&] {
+    le = cudaLaunchCooperativeKernel((const void*)k_cg32_persist, dim3(blocks), dim3(kPersistThreads), args,
+                                     smem, c->stream);
+  }));
+  if (le != cudaSuccess) return cuda_fail(c, le, "persistent CG launch");
+  return HMC_OK;
 }
 
 template <typename R>

@@ -57,6 +57,13 @@ bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt);
 // Whether the marching FP32 CG kernels' reduction partials fit their buffers
 // at `threads` cells and `tt` time slices per block.
 bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt);
+// The persistent FP32 CG kernel: whether its on-chip state fits this lattice,
+// and one cooperative launch that runs the whole solve from the state k_init0
+// (or the residual kernel) left in sc, x, r and p0 (p1: second direction
+// buffer, u: scratch).
+bool cg32_persist_ok(const hmc_ctx* c, const Geo& g);
+hmc_status cg32_persist_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1,
+                               float2* u, CGScal* sc);
 
 // Resident blocks per SM of a CG kernel at `threads` threads per block.
 int cg_kernel_occupancy(int id, int threads);

@@ -102,6 +102,24 @@ __device__ __forceinline__ PairOut<R> mdag_pair_ld(const Geo& g, Cx<R> za, Cx<R>
   return PairOut<R>{oa, ob};
 }
 
+// M at the cell-time of nb of the vector returned by the loader L (phases
+// from ph); used where the loads need a particular cache policy.
+template <typename R, typename PH, typename LD>
+__device__ __forceinline__ PairOut<R> m_pair_ld(const Geo& g, const PH& ph, R dm, const Nbr& nb, LD L) {
+  const int H = g.H;
+  const R dk = geo_dk(g, R(0));
+  Cx<R> ua = L(nb.q), ub = L(H + nb.q);
+  Cx<R> ea = ph(nb.q);
+  Cx<R> za = cneg_if(Cx<R>{ea.re - dm, ea.im}, nb.wrap_tm);
+  Cx<R> ta = cfma(za, L(nb.tm), Cx<R>{-ua.re, -ua.im});
+  Cx<R> oa = hopsum(ta, dk, ub, L(H + nb.im1), L(H + nb.jm1));
+  Cx<R> eb = ph(H + nb.q);
+  Cx<R> zb = cneg_if(Cx<R>{dm - eb.re, eb.im}, nb.wrap_tp);
+  Cx<R> tb = cfma(zb, L(H + nb.tp), ub);
+  Cx<R> ob = hopsum(tb, dk, ua, L(nb.ip1), L(nb.jp1));
+  return PairOut<R>{oa, ob};
+}
+
 // M applied at the cell-time of nb, reading u (precision R).
 template <typename R, typename PH = Phase<R>>
 __device__ __forceinline__ PairOut<R> m_pair(const Geo& g, const PH& ph, R dm,

@@ -49,6 +49,10 @@ static hmc_status vec_slots(hmc_ctx* c, V2<R>** r, V2<R>** p, V2<R>** u) {
 // precision. Results of later solves are reproducible for the chosen shape
 // (the shape fixes the reduction order).
 template <typename R>
+hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x, bool x_zero,
+                   double tol, int maxit, int sc_slot, bool want_true_res, SolveStats* st);
+
+template <typename R>
 static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
   bool& done = sizeof(R) == 4 ? c->tuned32 : c->tuned64;
   if (done) return HMC_OK;
@@ -140,6 +144,35 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
     }
   }
   for (int k = 0; k < nk; ++k) c->shape[ids[k]] = keep[k];
+  // FP32: the persistent kernel against the chosen pair, both through the
+  // solver path they would run in (48 iterations, twice each, best kept)
+  if constexpr (sizeof(R) == 4) {
+    c->persist32 = false;
+    if (c->cg32_variant == 0 && !c->capturing && cg32_persist_ok(c, g)) {
+      float tm[2] = {1e30f, 1e30f};
+      for (int k = 0; k < 2; ++k) {
+        c->persist32 = (k == 1);
+        for (int rep = 0; rep < 2; ++rep) {
+          SolveStats tmp;
+          HMC_CUDA(c, cudaEventRecord(e0, c->stream));
+          const hmc_status st = cg_core<R>(c, ms, sigma, b, x, true, 1e-30, 48, 2, false, &tmp);
+          HMC_CUDA(c, cudaEventRecord(e1, c->stream));
+          HMC_CUDA(c, cudaEventSynchronize(e1));
+          if (st != HMC_OK && st != HMC_ERR_NOT_CONVERGED) {
+            c->persist32 = false;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+          }
+          c->err.clear();
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          tm[k] = std::min(tm[k], t);
+        }
+      }
+      c->persist32 = tm[1] < tm[0];
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return HMC_OK;
@@ -190,8 +223,21 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   // (one per buffer set) unless per-kernel timing is on; the host reads the
   // state after 1, 1, 2, 4, 4, ... chunks.
   constexpr int kChunk = 8;
+  // FP32: the whole solve in one persistent launch when the tuner (or the
+  // pinned variant) chose it
+  bool persistent = false;
+  if constexpr (sizeof(R) == 4) {
+    persistent = !c->capturing && (c->cg32_variant == 4 || (c->cg32_variant == 0 && c->persist32)) &&
+                 cg32_persist_ok(c, g);
+    if (persistent) {
+      HMC_TRY(cg32_persist_launch(c, g, (float2*)x, (float2*)r, (float2*)p, (float2*)q, (float2*)u, sc));
+      HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
+      HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+      c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
+    }
+  }
   GraphEntry* ge = nullptr;
-  if (c->use_graphs && !c->prof.timing) {
+  if (!persistent && c->use_graphs && !c->prof.timing) {
     const void* key[6] = {sc, r, p, q, u, x};
     const int kind = sizeof(R) == 4 ? 32 : 64;
     ge = find_graph(c, kind, key);
@@ -211,7 +257,7 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   const int nk = sizeof(R) == 4 ? 2 : 3;
   int per_check = 1, checks = 0;
   long long launched = 0;
-  for (;;) {
+  for (; !persistent;) {
     for (int i = 0; i < per_check; ++i) {
       if (ge) {
         HMC_CUDA(c, cudaGraphLaunch(ge->exec, c->stream));
@@ -243,6 +289,7 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
     st->true_rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
     if (sizeof(R) == 8) st->applies64++; else st->applies32++;
   }
+  if (sch->done == CG_TIMEOUT) return fail(c, HMC_ERR_TIMEOUT, "persistent CG: a grid barrier wait gave up");
   if (sch->done == CG_BREAKDOWN) return fail(c, HMC_ERR_NAN, "CG breakdown: non-positive or non-finite curvature/residual");
   if (sch->done == CG_MAXIT) return fail(c, HMC_ERR_NOT_CONVERGED, "CG reached its iteration limit");
   return HMC_OK;

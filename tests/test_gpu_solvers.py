@@ -141,11 +141,12 @@ def test_fcg_mixed(name, ms):
         assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("name,ms,sigma,bound", [("C3", 0.0, 0.0, 1e-3), ("C3", 0.4, 0.05, 5e-5),
                                                  ("C5", 0.1, 0.0, 1e-3)])
 def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
-    """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching) solve
+    """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching,
+    persistent) solve
     to the single-precision floor, and FGMRES built on them meets 1e-10. The
     FP32 solution's true residual is bounded by the recursive tolerance plus
     the rounding drift, about eps_32 times the condition number (near 10^4 at
@@ -159,7 +160,9 @@ def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
         shapes = ctx.profile_read()
         x, finfo = ctx.solve_fgmres(dev(w.phi), ms, dev(w.b), sigma=sigma, tol=1e-10, a=1.0)
     waves = shapes["cg_pMdag_f32"]["waves"]
-    assert {1: waves >= 0, 2: -1000 < waves < 0, 3: waves <= -1000}[variant]
+    persist = shapes["cg_persist_f32"]["launches"]
+    assert {1: waves >= 0, 2: -1000 < waves < 0, 3: waves <= -1000, 4: True}[variant]
+    assert (persist > 0) == (variant == 4)
     b32 = w.b.astype(np.complex64).astype(np.complex128)
     assert info["iters"] > 0 and info["status"] == 0
     assert true_rel(ol, w.phi, ms, sigma, host(x32).astype(np.complex128), b32) < bound

@@ -287,6 +287,15 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
  * Setting it re-runs the tuner at the next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
+/* Test hook for the bounded waits of the persistent FP32 CG kernel (variant 4
+ * above): from the next persistent solve on, every grid barrier waits for
+ * `extra` more arrivals than the launch has blocks (with extra > 0 no barrier
+ * can complete, a wait that nothing ends) and gives up after `limit_cycles`
+ * SM clock cycles (0: the default, about one second). A solve whose wait gave
+ * up returns HMC_ERR_TIMEOUT and the context stays usable. extra = 0 and
+ * limit_cycles = 0 restore normal operation. */
+hmc_status hmc_set_wait_test(hmc_ctx* ctx, int extra, long long limit_cycles);
+
 /* ---- instrumentation ------------------------------------------------------- */
 
 #define HMC_NKERNELS 32

@@ -294,6 +294,12 @@ class Context:
         3: marching; 4: persistent (one cooperative launch per solve)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
+    def set_wait_test(self, extra: int, limit_cycles: int = 0):
+        """Test hook: grid barriers of the persistent FP32 CG kernel wait for
+        `extra` more arrivals than there are blocks and give up after
+        `limit_cycles` SM cycles (0: default); (0, 0) restores normal work."""
+        self._check(self.lib.hmc_set_wait_test(self.h, extra, limit_cycles))
+
     # --- instrumentation ----------------------------------------------------
     def profile(self, timing: bool, reset: bool = True):
         self._check(self.lib.hmc_profile(self.h, 1 if timing else 0, 1 if reset else 0))

@@ -436,6 +436,14 @@ hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   return HMC_OK;
 }
 
+hmc_status hmc_set_wait_test(hmc_ctx* c, int extra, long long limit_cycles) {
+  if (!c) return HMC_ERR_INVALID;
+  if (extra < 0 || limit_cycles < 0) return fail(c, HMC_ERR_INVALID, "extra and limit_cycles must be >= 0");
+  c->bar_extra = extra;
+  c->bar_limit = limit_cycles;
+  return HMC_OK;
+}
+
 hmc_status hmc_profile(hmc_ctx* c, int timing_on, int reset) {
   if (!c) return HMC_ERR_INVALID;
   if (reset) {

@@ -136,6 +136,8 @@ struct hmc_ctx {
   int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching,
                          // 4 persistent
   bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
+  int bar_extra = 0;         // test hook: extra arrivals every grid barrier waits for
+  long long bar_limit = 0;   // test hook: barrier wait limit in SM cycles (0: default)
 
   bool use_graphs = true;
   bool capturing = false;

@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
     k_cg32_persist(Geo g, Phase<float> ph, float2* __restrict__ x, float2* __restrict__ r,
                    float2* __restrict__ p0, float2* __restrict__ p1, float2* __restrict__ u, CGScal* sc,
                    float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
-                   int ipb) {
+                   int ipb, unsigned expect) {
   extern __shared__ float4 s_state[];
   float4* sx = s_state;         // x at the block's cell-times: (A.re, A.im, B.re, B.im)
   float4* sp = s_state + ipb;   // p
@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
       const float2 v = ff_block_sum(make_float2(loc, 0.f));
       if (threadIdx.x == 0) partA[blockIdx.x] = v;
     }
-    if (!grid_barrier(gb, gridDim.x, limit)) {
+    if (!grid_barrier(gb, expect, limit)) {
       done = CG_TIMEOUT;
       break;
     }
@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
       const float2 v = ff_block_sum(make_float2(loc, 0.f));
       if (threadIdx.x == 0) partB[blockIdx.x] = v;
     }
-    if (!grid_barrier(gb, gridDim.x, limit)) {
+    if (!grid_barrier(gb, expect, limit)) {
       done = CG_TIMEOUT;
       break;
     }
@@ -1110,9 +1110,10 @@ hmc_status cg32_persist_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, f
   float2* pb = (float2*)c->partB;
   GridBar* gb = c->gbar;
   // about one second of SM clock per barrier wait before giving up
-  long long limit = 2000000000LL;
+  long long limit = c->bar_limit > 0 ? c->bar_limit : 2000000000LL;
+  unsigned expect = (unsigned)blocks + (unsigned)c->bar_extra;  // arrivals a barrier waits for
   Geo gg = g;
-  void* args[] = {&gg, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &ipb};
+  void* args[] = {&gg, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &ipb, &expect};
   cudaError_t le = cudaSuccess;
   HMC_TRY(launch_b(c, K_CG_PERSIST32, 0.0, [&] {
     le = cudaLaunchCooperativeKernel((const void*)k_cg32_persist, dim3(blocks), dim3(kPersistThreads), args,

@@ -93,3 +93,38 @@ def test_bad_batched_descriptor():
             ctx.solve_batched([bad])
         infos = ctx.solve_batched([good])
         assert infos[0]["true_rel_res"] <= 1e-10
+
+
+def test_bounded_grid_barrier_wait_times_out_and_context_survives():
+    """The persistent FP32 CG kernel's grid barriers wait a bounded number of SM
+    cycles: with the test hook making every barrier wait for one arrival that
+    never comes, the solve returns HMC_ERR_TIMEOUT after about a millisecond,
+    and the same context then solves normally, agreeing with the two-kernel
+    CG (both meet the tolerance up to FP32 rounding drift)."""
+    need_gpu()
+    import time
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C1")
+    b32 = dev(w.b.astype(np.complex64))
+    with ctx_for(w.lat) as ref:
+        ref.set_cg_variant(1)
+        x_ref, _ = ref.solve_spcg(dev(w.phi), 0.3, b32, tol=1e-6)
+    with ctx_for(w.lat) as ctx:
+        ctx.set_cg_variant(4)
+        ctx.set_wait_test(1, 2_000_000)
+        t = time.perf_counter()
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_spcg(dev(w.phi), 0.3, b32, tol=1e-6)
+        assert e.value.status == hmc._abi.HMC_ERR_TIMEOUT
+        assert time.perf_counter() - t < 30.0
+        ctx.set_wait_test(0, 0)
+        x, info = ctx.solve_spcg(dev(w.phi), 0.3, b32, tol=1e-6)
+        assert info["status"] == 0
+        assert ctx.profile_read()["cg_persist_f32"]["launches"] == 2
+    from oracle import fermion as of
+    from oracle.lattice import Lattice as OLat
+    ol = OLat.from_params(w.lat)
+    b = w.b.astype(np.complex64).astype(np.complex128)
+    for xs in (host(x_ref), host(x)):
+        r = b - of.apply_MMdag(ol, w.phi, 0.3, xs.astype(np.complex128))
+        assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b)

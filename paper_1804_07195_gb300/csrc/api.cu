@@ -267,6 +267,10 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   if (c->tickets) cudaFree(c->tickets);
   if (c->sc) cudaFree(c->sc);
   if (c->gbar) cudaFree(c->gbar);
+  for (int i = 0; i < hmc_ctx::kBatchSlots; ++i)
+    if (c->bpool[i]) cudaFree(c->bpool[i]);
+  for (int i = 0; i < 4; ++i)
+    if (c->bpool_host[i]) cudaFreeHost(c->bpool_host[i]);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->dscal) cudaFree(c->dscal);
   if (c->dscal_host) cudaFreeHost(c->dscal_host);

@@ -184,12 +184,15 @@ __global__ void kb_init(const BSys* __restrict__ sys, const int* __restrict__ bs
   }
 }
 
+// p_new = r + beta p_old (beta = 0 on a system's first iteration), evaluated
+// at every stencil point it reads; u = M^dagger p_new; per-system <p, A p>.
 template <typename R>
-__global__ void __launch_bounds__(512) kb_cg_mdag(const BSys* __restrict__ sys, const int* __restrict__ bsys,
-                                                  BState* bst, const double2* __restrict__ E,
-                                                  const float* __restrict__ p32, const V2<R>* __restrict__ p,
-                                                  V2<R>* __restrict__ u, double* partials, unsigned* tickets,
-                                                  unsigned* ndone) {
+__global__ void __launch_bounds__(512) kb_cg_pmdag(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                   BState* bst, const double2* __restrict__ E,
+                                                   const float* __restrict__ p32, const V2<R>* __restrict__ r,
+                                                   const V2<R>* __restrict__ pold, V2<R>* __restrict__ pnew,
+                                                   V2<R>* __restrict__ u, double* partials, unsigned* tickets,
+                                                   unsigned* ndone) {
   BLOCK_SYS();
   __shared__ BScal<R> sc;
   __shared__ int skip;
@@ -197,21 +200,35 @@ __global__ void __launch_bounds__(512) kb_cg_mdag(const BSys* __restrict__ sys, 
     skip = bst[s_].cg.done;
     sc.dm = (R)S_.dm;
     sc.sigma = (R)S_.sigma;
+    sc.coef = (R)bst[s_].cg.beta;
   }
   __syncthreads();
   if (skip) return;
   const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
-  const R dm = sc.dm, sigma = sc.sigma;
-  const V2<R>* ps = p + S_.off;
+  const R dm = sc.dm, sigma = sc.sigma, beta = sc.coef, dk = geo_dk(g, R(0));
+  const V2<R>* rs = r + S_.off;
+  const V2<R>* pos = pold + S_.off;
+  V2<R>* pns = pnew + S_.off;
   V2<R>* us = u + S_.off;
+  auto P = [&](int k) {
+    const Cx<R> a = ld<R>(rs, k), bb = ld<R>(pos, k);
+    return Cx<R>{fma(beta, bb.re, a.re), fma(beta, bb.im, a.im)};
+  };
   R loc = 0;
   for (int q = lb * blockDim.x + threadIdx.x; q < g.H; q += stride) {
-    Nbr nb = neighbours(g, q);
-    PairOut<R> o = mdag_pair<R>(g, ph, dm, ps, nb);
+    const Nbr nb = neighbours(g, q);
+    const Cx<R> ea = ph(nb.tp);
+    const Cx<R> za = cneg_if(Cx<R>{ea.re - dm, -ea.im}, nb.wrap_tp);
+    const Cx<R> eb = ph(g.H + nb.tm);
+    const Cx<R> zb = cneg_if(Cx<R>{dm - eb.re, -eb.im}, nb.wrap_tm);
+    const PairOut<R> o = mdag_pair_ld<R>(g, za, zb, dk, nb, P);
+    const Cx<R> pa = P(q), pb = P(g.H + q);
+    st(pns, q, pa);
+    st(pns, g.H + q, pb);
     st(us, q, o.a);
     st(us, g.H + q, o.b);
     loc += norm2(o.a) + norm2(o.b);
-    if (sigma != (R)0) loc += sigma * (norm2(ld<R>(ps, q)) + norm2(ld<R>(ps, g.H + q)));
+    if (sigma != (R)0) loc += sigma * (norm2(pa) + norm2(pb));
   }
   const double bt = block_total(loc);
   double tot;
@@ -284,29 +301,6 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
     else if (c.iter >= c.maxit)
       c.done = CG_MAXIT;
     if (c.done) atomicAdd(ndone, 1u);
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(512) kb_cg_p(const BSys* __restrict__ sys, const int* __restrict__ bsys,
-                                               const BState* bst, const V2<R>* __restrict__ r,
-                                               V2<R>* __restrict__ p) {
-  BLOCK_SYS();
-  __shared__ R sbeta;
-  __shared__ int skip;
-  if (threadIdx.x == 0) {
-    skip = bst[s_].cg.done;
-    sbeta = (R)bst[s_].cg.beta;
-  }
-  __syncthreads();
-  if (skip) return;
-  const R beta = sbeta;
-  for (int k = lb * blockDim.x + threadIdx.x; k < g.N; k += stride) {
-    const long long i = S_.off + k;
-    Cx<R> rk = ld<R>(r, i), pk = ld<R>(p, i);
-    pk.re = fma(beta, pk.re, rk.re);
-    pk.im = fma(beta, pk.im, rk.im);
-    st(p, i, pk);
   }
 }
 
@@ -390,28 +384,51 @@ struct BatchWs {
   unsigned* ndone = nullptr;
   unsigned* ndone_host = nullptr;
   double* partials = nullptr;
-  double2 *E = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *u = nullptr;
+  double2 *E = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
   float *phi32 = nullptr;
-  float2 *r32 = nullptr, *e32 = nullptr, *p32v = nullptr, *u32 = nullptr, *rr32 = nullptr;
+  float2 *r32 = nullptr, *e32 = nullptr, *p32v = nullptr, *q32v = nullptr, *u32 = nullptr, *rr32 = nullptr;
+  int nalloc = 0;  // pool slots taken by this call
   std::vector<void*> allocs;
 };
 
+// Device buffers come from the context's pool: the i-th request of a call
+// takes slot i, reallocated only when it is too small for this batch.
 static hmc_status bmalloc(hmc_ctx* c, BatchWs& w, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, HMC_ERR_NOMEM, "batched workspace allocation failed");
+  if (bytes < 16) bytes = 16;
+  const int slot = w.nalloc++;
+  if (slot >= hmc_ctx::kBatchSlots) return fail(c, HMC_ERR_NOMEM, "batched workspace: too many buffers");
+  if (c->bpool_bytes[slot] < bytes) {
+    if (c->bpool[slot]) cudaFree(c->bpool[slot]);
+    c->bpool[slot] = nullptr;
+    c->bpool_bytes[slot] = 0;
+    cudaError_t e = cudaMalloc(&c->bpool[slot], bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->bpool[slot] = nullptr;
+      return fail(c, HMC_ERR_NOMEM, "batched workspace allocation failed");
+    }
+    c->bpool_bytes[slot] = bytes;
   }
-  w.allocs.push_back(*p);
+  *p = c->bpool[slot];
+  return HMC_OK;
+}
+
+// Pinned host mirrors, also pooled (slot 0: states, 1: residual norms, 2: count).
+static hmc_status bmalloc_host(hmc_ctx* c, int slot, void** p, size_t bytes) {
+  if (c->bpool_host_bytes[slot] < bytes) {
+    if (c->bpool_host[slot]) cudaFreeHost(c->bpool_host[slot]);
+    c->bpool_host[slot] = nullptr;
+    c->bpool_host_bytes[slot] = 0;
+    HMC_CUDA(c, cudaMallocHost(&c->bpool_host[slot], bytes));
+    c->bpool_host_bytes[slot] = bytes;
+  }
+  *p = c->bpool_host[slot];
   return HMC_OK;
 }
 
 static void bfree(BatchWs& w) {
-  for (void* p : w.allocs) cudaFree(p);
+  // pooled buffers stay with the context
   w.allocs.clear();
-  if (w.st_host) cudaFreeHost(w.st_host);
-  if (w.rrbb_host) cudaFreeHost(w.rrbb_host);
-  if (w.ndone_host) cudaFreeHost(w.ndone_host);
   w.st_host = nullptr;
   w.rrbb_host = nullptr;
   w.ndone_host = nullptr;
@@ -438,12 +455,17 @@ static int plan_blocks(BatchWs& w, int threads, int ipt) {
 }
 
 // Kernel sequence of one CG iteration for all systems, in precision R.
+// (iteration i reads the direction from p when i is even and from q when odd,
+// and writes the new one into the other buffer)
 template <typename R>
-static void cg_iteration(const BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p, V2<R>* u) {
+static void cg_iteration(const BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p, V2<R>* q, V2<R>* u,
+                         int i) {
   const dim3 G(w.blocks), T(w.threads);
-  kb_cg_mdag<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, p, u, w.partials, w.tickets, w.ndone);
-  kb_cg_m<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, u, p, x, r, w.partials, w.tickets, w.ndone);
-  kb_cg_p<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, r, p);
+  V2<R>* pold = (i & 1) ? q : p;
+  V2<R>* pnew = (i & 1) ? p : q;
+  kb_cg_pmdag<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, r, pold, pnew, u, w.partials, w.tickets,
+                                  w.ndone);
+  kb_cg_m<R><<<G, T, 0, s>>>(w.sys, w.bsys, w.st, w.E, w.phi32, u, pnew, x, r, w.partials, w.tickets, w.ndone);
 }
 
 // Tuned (threads, cell-times per thread) per precision and size bucket.
@@ -464,7 +486,7 @@ static hmc_status upload_plan(hmc_ctx* c, BatchWs& w, cudaStream_t s) {
 // keep the fastest for the (precision, size) bucket.
 template <typename R>
 static hmc_status autotune(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p,
-                           V2<R>* u, const V2<R>* b, int* threads, int* ipt) {
+                           V2<R>* q, V2<R>* u, const V2<R>* b, int* threads, int* ipt) {
   const int bucket = (int)std::log2((double)std::max<long long>(w.Ntot, 2));
   TuneKey key{(int)sizeof(R), bucket};
   auto it = g_tuned.find(key);
@@ -485,9 +507,9 @@ static hmc_status autotune(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<
     HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * w.nsys, s));
     kb_init<R><<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.st, w.tol2, b, x, r, p, 1 << 30,
                                                w.partials, w.tickets);
-    cg_iteration<R>(w, s, x, r, p, u);
+    cg_iteration<R>(w, s, x, r, p, q, u, 0);
     HMC_CUDA(c, cudaEventRecord(e0, s));
-    for (int i = 0; i < 3; ++i) cg_iteration<R>(w, s, x, r, p, u);
+    for (int i = 1; i < 4; ++i) cg_iteration<R>(w, s, x, r, p, q, u, i);
     HMC_CUDA(c, cudaEventRecord(e1, s));
     HMC_CUDA(c, cudaEventSynchronize(e1));
     HMC_CUDA(c, cudaGetLastError());
@@ -511,7 +533,7 @@ static hmc_status autotune(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<
 // replaying a captured graph of `chunk` iterations.
 template <typename R>
 static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>* b, V2<R>* x, V2<R>* r,
-                             V2<R>* p, V2<R>* u, int maxit, int nactive, long long* iters_launched) {
+                             V2<R>* p, V2<R>* q, V2<R>* u, int maxit, int nactive, long long* iters_launched) {
   HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * w.nsys, s));
   HMC_CUDA(c, cudaMemsetAsync(w.ndone, 0, sizeof(unsigned), s));
   kb_init<R><<<w.blocks, w.threads, 0, s>>>(w.sys, w.bsys, w.st, w.tol2, b, x, r, p, maxit, w.partials,
@@ -528,7 +550,7 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   HMC_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < chunk; ++i) cg_iteration<R>(w, s, x, r, p, u);
+  for (int i = 0; i < chunk; ++i) cg_iteration<R>(w, s, x, r, p, q, u, i);  // even chunk: p holds the newest
   HMC_CUDA(c, cudaStreamEndCapture(s, &graph));
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   if (e != cudaSuccess) {
@@ -538,23 +560,28 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   hmc_status status = HMC_OK;
   long long launched = 0;
   const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
-  const double bytes_iter = sizeof(R) == 8 ? 192.0 : 96.0;
+  const double bytes_iter = sizeof(R) == 8 ? 192.0 : 88.0;
   std::vector<char> running(w.nsys);
   for (int i = 0; i < w.nsys; ++i) running[i] = w.st_host[i].cg.done == CG_RUNNING;
+  // the host reads the states after 1, 1, 2, 4, 4, ... chunks
+  int per_check = 1, checks = 0;
   for (;;) {
     double act = 0.0;
     for (int i = 0; i < w.nsys; ++i) act += running[i] ? (double)w.hsys[i].g.N : 0.0;
-    c->prof.bytes[kid] += act * bytes_iter * chunk;
-    cudaEvent_t a = nullptr;
-    prof_begin(c, kid, &a);
-    e = cudaGraphLaunch(exec, s);
-    prof_end(c, kid, a);
-    c->prof.launches[kid] += 3 * chunk - 1;
+    for (int k = 0; k < per_check && e == cudaSuccess; ++k) {
+      c->prof.bytes[kid] += act * bytes_iter * chunk;
+      cudaEvent_t a = nullptr;
+      prof_begin(c, kid, &a);
+      e = cudaGraphLaunch(exec, s);
+      prof_end(c, kid, a);
+      c->prof.launches[kid] += 2 * chunk - 1;
+      launched += chunk;
+    }
     if (e != cudaSuccess) {
       status = cuda_fail(c, e, "cudaGraphLaunch");
       break;
     }
-    launched += chunk;
+    if (++checks >= 2 && per_check < 4) per_check *= 2;
     e = cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -649,18 +676,20 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
     HMC_TRY(bmalloc(c, w, (void**)&w.r, sizeof(double2) * Nt));
     if (!mixed) {
       HMC_TRY(bmalloc(c, w, (void**)&w.p, sizeof(double2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.q, sizeof(double2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.u, sizeof(double2) * Nt));
     } else {
       HMC_TRY(bmalloc(c, w, (void**)&w.u, sizeof(double2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.r32, sizeof(float2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.e32, sizeof(float2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.p32v, sizeof(float2) * Nt));
+      HMC_TRY(bmalloc(c, w, (void**)&w.q32v, sizeof(float2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.u32, sizeof(float2) * Nt));
       HMC_TRY(bmalloc(c, w, (void**)&w.rr32, sizeof(float2) * Nt));
     }
-    HMC_CUDA(c, cudaMallocHost(&w.st_host, sizeof(BState) * nsys));
-    HMC_CUDA(c, cudaMallocHost(&w.rrbb_host, sizeof(double) * 2 * nsys));
-    HMC_CUDA(c, cudaMallocHost(&w.ndone_host, sizeof(unsigned)));
+    HMC_TRY(bmalloc_host(c, 0, (void**)&w.st_host, sizeof(BState) * nsys));
+    HMC_TRY(bmalloc_host(c, 1, (void**)&w.rrbb_host, sizeof(double) * 2 * nsys));
+    HMC_TRY(bmalloc_host(c, 2, (void**)&w.ndone_host, sizeof(unsigned)));
     HMC_CUDA(c, cudaMemsetAsync(w.tickets, 0, sizeof(unsigned) * nsys, s));
     // gather b, phases
     for (int i = 0; i < nsys; ++i)
@@ -687,11 +716,11 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
     if (!mixed) {
       for (int i = 0; i < nsys; ++i) tol2[i] = sys[i].tol * sys[i].tol;
       HMC_CUDA(c, cudaMemcpyAsync(w.tol2, tol2.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s));
-      HMC_TRY(autotune<double>(c, w, s, w.x, w.r, w.p, w.u, w.b, &threads, &ipt));
+      HMC_TRY(autotune<double>(c, w, s, w.x, w.r, w.p, w.q, w.u, w.b, &threads, &ipt));
       plan_blocks(w, threads, ipt);
       HMC_TRY(upload_plan<double>(c, w, s));
       HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
-      HMC_TRY(batched_cg<double>(c, w, s, w.b, w.x, w.r, w.p, w.u, maxit, nsys, &launched));
+      HMC_TRY(batched_cg<double>(c, w, s, w.b, w.x, w.r, w.p, w.q, w.u, maxit, nsys, &launched));
       HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s));
       HMC_CUDA(c, cudaStreamSynchronize(s));
       for (int i = 0; i < nsys; ++i) {
@@ -742,13 +771,13 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
         HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
         if (!tuned) {
           // r32 now holds the first right-hand sides: tune the FP32 block shape on them
-          HMC_TRY(autotune<float>(c, w, s, w.e32, w.rr32, w.p32v, w.u32, w.r32, &threads, &ipt));
+          HMC_TRY(autotune<float>(c, w, s, w.e32, w.rr32, w.p32v, w.q32v, w.u32, w.r32, &threads, &ipt));
           plan_blocks(w, threads, ipt);
           HMC_TRY(upload_plan<float>(c, w, s));
           HMC_CUDA(c, cudaMemcpyAsync(w.st, init.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s));
           tuned = true;
         }
-        HMC_TRY(batched_cg<float>(c, w, s, w.r32, w.e32, w.rr32, w.p32v, w.u32, 2000, nact, &launched));
+        HMC_TRY(batched_cg<float>(c, w, s, w.r32, w.e32, w.rr32, w.p32v, w.q32v, w.u32, 2000, nact, &launched));
         HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s));
         HMC_CUDA(c, cudaStreamSynchronize(s));
         for (int i = 0; i < nsys; ++i) {

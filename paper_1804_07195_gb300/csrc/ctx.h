@@ -136,6 +136,13 @@ struct hmc_ctx {
   int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching,
                          // 4 persistent
   bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
+  // device and pinned host buffers of the batched solver, kept across calls
+  // (slot i holds the i-th buffer a call asks for; grown when too small)
+  static constexpr int kBatchSlots = 40;
+  void* bpool[kBatchSlots] = {};
+  size_t bpool_bytes[kBatchSlots] = {};
+  void* bpool_host[4] = {};
+  size_t bpool_host_bytes[4] = {};
   int bar_extra = 0;         // test hook: extra arrivals every grid barrier waits for
   long long bar_limit = 0;   // test hook: barrier wait limit in SM cycles (0: default)
 

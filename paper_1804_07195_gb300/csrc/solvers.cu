@@ -528,7 +528,6 @@ hmc_status fcg_core(hmc_ctx* c, double ms, double sigma, const double2* b, doubl
   const int N = c->geo.N;
   const size_t vb = sizeof(double2) * (size_t)N;
   double2 *r, *z, *buf, *u;
-  float2* v32 = nullptr;
   HMC_TRY(ws_get(c, WS_FG_R, vb, (void**)&r));
   HMC_TRY(ws_get(c, WS_FG_W, vb, (void**)&z));
   HMC_TRY(ws_get(c, WS_FG_V, vb * 4, (void**)&buf));

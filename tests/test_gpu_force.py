@@ -104,3 +104,36 @@ def test_gaussian_term_only():
         S, _ = ctx.action(dev(w.phi), [], [], flags=1)
     assert rel_max(host(g), oa.grad_gaussian(ol, w.phi)) <= 1e-15
     assert abs(S - oa.gaussian_action(ol, w.phi)) <= 1e-12 * S
+
+
+@pytest.mark.slow
+def test_force_at_full_size_is_the_action_derivative():
+    """102x102x64 with the three Hasenbusch masses, mixed-precision solves at
+    1e-13: the force dS/dphi (all terms) agrees with central differences of
+    the action along random unit directions, within the rounding of the
+    differences plus 1e-6 relative. The rounding allowance is 40 eps |S| / h:
+    each action is a sum of 1.3M terms reduced in a tree of depth about 20.
+    A property that holds at any size; the oracle cannot form this lattice's
+    solves."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.workload("C5")
+    masses = list(w.masses)
+    opts = hmc.SolverOpts(method=hmc._abi.HMC_SOLVER_FGMRES_MIXED, tol=1e-13, maxit=200000)
+    eps = np.finfo(np.float64).eps
+    with ctx_for(w.lat) as ctx:
+        phi = dev(w.phi)
+        chis, _ = ctx.make_chi(phi, masses, [dev(r) for r in w.rho], opts=opts)
+        F, _ = ctx.force(phi, masses, chis, opts=opts)
+        S0, _ = ctx.action(phi, masses, chis, opts=opts)
+        rng = np.random.default_rng(5)
+        for _ in range(2):
+            d = rng.normal(size=w.lat.nsites)
+            d /= np.linalg.norm(d)
+            dd = dev(d)
+            an = float((F * dd).sum())
+            h = 1e-3
+            Sp, _ = ctx.action(phi + h * dd, masses, chis, opts=opts)
+            Sm, _ = ctx.action(phi - h * dd, masses, chis, opts=opts)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - an) <= 1e-6 * abs(an) + 40 * eps * abs(S0) / h, (fd, an, S0)

@@ -114,7 +114,7 @@ def cpu_oracle_apply(seconds: float):
     import workloads as W
     from oracle import fermion
     from oracle.lattice import Lattice
-    w = W.workload("C5")
+    w = W.workload("L102x102x64")
     lat = Lattice.from_params(w.lat)
     reps = 0
     t0 = time.perf_counter()
@@ -196,19 +196,19 @@ def main():
 
     build.build()
     dev = torch.device("cuda", local)
-    w0 = W.workload("C5")
+    w0 = W.workload("L102x102x64")
     p = w0.lat
     lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
     N = lat.nsites
-    masses = list(W.C5_MASSES)
-    integ = hmc.Integrator(0, W.C5_NMD, W.C5_NI, W.OMELYAN_ZETA, 1.0)
+    masses = list(W.L102_MASSES)
+    integ = hmc.Integrator(0, W.L102_NMD, W.L102_NI, W.OMELYAN_ZETA, 1.0)
     md_opts = hmc.SolverOpts(method=1, tol=1e-10, a=args.fgmres_a)
     act_opts = hmc.SolverOpts(method=1, tol=1e-12, a=args.fgmres_a)
 
     nsteps_total = args.warmup + args.steps + 1 + args.e2e_steps
 
     def step_inputs(k):
-        g = W.rng(replica_seed(W.SEEDS["C5"], rank, k))
+        g = W.rng(replica_seed(W.SEEDS["L102x102x64"], rank, k))
         pi = W.draw_pi(g, N)
         rho = [W.draw_complex(g, N) for _ in range(len(masses) + 1)]
         return pi, rho
@@ -353,7 +353,7 @@ def main():
 
     # the batched workload: 48 uneven lattices x 3 masses = 144 systems at 1e-10,
     # batched mixed vs batched FP64 vs FP64 CG one system at a time
-    solve["c4_batched"] = batched_solve_times(hmc, W, torch, stream, flush)
+    solve["batched_48_lattices"] = batched_solve_times(hmc, W, torch, stream, flush)
     solve["apply"] = apply_rates(hmc, W, torch, stream, flush, hbm)
 
     # end to end through the public API with host buffers
@@ -464,7 +464,7 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
 
 def batched_solve_times(hmc, W, torch, stream, flush):
     systems, ctxs = [], {}
-    for w in W.c4_instances():
+    for w in W.batch_instances():
         p = w.lat
         lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
         key = (p.n, p.m, p.nt)
@@ -546,7 +546,7 @@ def kernel_case(case):
     build.build()
     if case == "batched":
         sys_ = []
-        for w in W.c4_instances():
+        for w in W.batch_instances():
             p = w.lat
             lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
             for ms, b in zip(w.masses, w.rho):
@@ -558,7 +558,7 @@ def kernel_case(case):
         print(json.dumps({"case": case, "systems": len(infos),
                           "max_true_rel_res": max(i["true_rel_res"] for i in infos)}))
         return
-    w = W.workload("C5")
+    w = W.workload("L102x102x64")
     p = w.lat
     lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
     phi = torch.tensor(w.phi, device="cuda")

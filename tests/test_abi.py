@@ -22,7 +22,7 @@ def lib():
     return ctypes.CDLL(path)
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_hot_path_calls():
     names = header_functions()
     for f in ("hmc_apply_M", "hmc_apply_Mdag", "hmc_solve_cg", "hmc_solve_fgmres", "hmc_force",
               "hmc_md_trajectory"):

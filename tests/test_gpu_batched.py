@@ -66,11 +66,11 @@ def test_batched_matches_single_solves():
 
 
 @pytest.mark.parametrize("mixed", [1, 0])
-def test_c4_workload(mixed):
+def test_batch_of_48_lattices(mixed):
     """48 instances, L in {6..36}, nt in {16,32,48}, 3 shifts each: 144 systems."""
     need_gpu()
     inst = []
-    for w in W.c4_instances():
+    for w in W.batch_instances():
         for ms, b in zip(w.masses, w.rho):
             inst.append((w, ms, 0.0, b))
     xs, infos = run_batch(inst, mixed)

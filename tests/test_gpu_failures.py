@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def test_nan_in_field_is_reported_and_context_survives():
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     bad = w.phi.copy()
     bad[17] = np.nan
     with ctx_for(w.lat) as ctx:
@@ -32,7 +32,7 @@ def test_nan_in_field_is_reported_and_context_survives():
 def test_nan_in_rhs_is_reported():
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     b = w.b.copy()
     b[3] = complex(np.nan, 0.0)
     with ctx_for(w.lat) as ctx:
@@ -44,7 +44,7 @@ def test_nan_in_rhs_is_reported():
 def test_spcg_iteration_limit():
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     with ctx_for(w.lat) as ctx:
         with pytest.raises(hmc.HMCError) as e:
             ctx.solve_spcg(dev(w.phi), 0.0, dev(w.b.astype(np.complex64)), tol=1e-7, maxit=3)
@@ -104,7 +104,7 @@ def test_bounded_grid_barrier_wait_times_out_and_context_survives():
     need_gpu()
     import time
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     b32 = dev(w.b.astype(np.complex64))
     with ctx_for(w.lat) as ref:
         ref.set_cg_variant(1)

@@ -21,7 +21,7 @@ def tight(method=0):
 @pytest.mark.parametrize("ms", [0.0, 0.5])
 def test_single_term_force_matches_dense_oracle(ms):
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     ol = OLat.from_params(w.lat)
     ref = oa.grad_pf_action(ol, w.phi, ms, w.b, oa.SolveA(ol, "dense"))
     with ctx_for(w.lat) as ctx:
@@ -35,11 +35,11 @@ def test_single_term_force_matches_dense_oracle(ms):
 
 
 @pytest.mark.parametrize("method", [0, 1])
-def test_hasenbusch_chi_action_and_force_C2(method):
+def test_hasenbusch_chi_action_and_force_12x12(method):
     """12x12, nt=32 with masses (0.3, 1.0): chi creation, S_i and dS/dphi from
     the GPU against the oracle with sparse-LU solves; rel. error <= 1e-7."""
     need_gpu()
-    w = W.workload("C2")
+    w = W.workload("L12x12x32")
     ol = OLat.from_params(w.lat)
     masses = list(w.masses)
     solve = oa.SolveA(ol, "splu")
@@ -62,12 +62,12 @@ def test_hasenbusch_chi_action_and_force_C2(method):
     assert abs(S - S_ref) <= 1e-10 * abs(S_ref)
 
 
-def test_autograd_force_vs_finite_differences_C2():
+def test_autograd_force_vs_finite_differences_12x12():
     """PseudofermionAction: backward equals central finite differences of the
     forward (h = 1e-6) along random directions, rel. error <= 1e-7."""
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C2")
+    w = W.workload("L12x12x32")
     masses = list(w.masses)
     with ctx_for(w.lat) as ctx:
         phi = dev(w.phi)
@@ -97,7 +97,7 @@ def test_autograd_force_vs_finite_differences_C2():
 
 def test_gaussian_term_only():
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     ol = OLat.from_params(w.lat)
     with ctx_for(w.lat) as ctx:
         g, _ = ctx.force(dev(w.phi), [], [], flags=1)
@@ -117,7 +117,7 @@ def test_force_at_full_size_is_the_action_derivative():
     solves."""
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C5")
+    w = W.workload("L102x102x64")
     masses = list(w.masses)
     opts = hmc.SolverOpts(method=hmc._abi.HMC_SOLVER_FGMRES_MIXED, tol=1e-13, maxit=200000)
     eps = np.finfo(np.float64).eps

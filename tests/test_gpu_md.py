@@ -51,7 +51,7 @@ def test_trajectory_matches_oracle(shape, masses, nmd, N, integ):
 def test_mixed_precision_trajectory_matches_fp64():
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     masses = [0.3, 1.0]
     w = W.small(6, 6, 16, seed=1001, masses=masses, U=2.0, beta=4.0)
     res = []
@@ -76,9 +76,9 @@ def test_c5_trajectory_mixed_vs_fp64_delta_H():
     error is second order in the solve residual."""
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C5")
+    w = W.workload("L102x102x64")
     masses = list(w.masses)
-    integ = hmc.Integrator(0, W.C5_NMD, W.C5_NI, W.OMELYAN_ZETA, 1.0)
+    integ = hmc.Integrator(0, W.L102_NMD, W.L102_NI, W.OMELYAN_ZETA, 1.0)
     out = []
     for method in (1, 0):
         with ctx_for(w.lat) as ctx:

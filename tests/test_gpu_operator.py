@@ -47,7 +47,7 @@ def test_apply_fp32(shape):
 
 def test_loaded_field_matches_explicit_field():
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     with ctx_for(w.lat) as ctx:
         phi, b = dev(w.phi), dev(w.b)
         ref = host(ctx.apply_MMdag(phi, 0.1, b, 0.0))
@@ -61,7 +61,7 @@ def test_largest_workload_sampled_rows():
     """102x102, nt=64 (1.33M sites): rows sampled across the lattice, including
     every wrap, against the oracle's stencil formula evaluated row by row."""
     need_gpu()
-    w = W.workload("C5")
+    w = W.workload("L102x102x64")
     lat = w.lat
     ol = OLat.from_params(lat)
     with ctx_for(lat) as ctx:

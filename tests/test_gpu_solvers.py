@@ -18,7 +18,7 @@ def true_rel(ol, phi, ms, sigma, x, b):
     return osv.true_rel_residual(lambda v: of.apply_MMdag(ol, phi, ms, v, sigma), x, b)
 
 
-@pytest.mark.parametrize("name,ms,sigma", [("C1", 0.0, 0.0), ("C1", 0.3, 0.0), ("C1", 0.0, 0.09)])
+@pytest.mark.parametrize("name,ms,sigma", [("L6x6x16", 0.0, 0.0), ("L6x6x16", 0.3, 0.0), ("L6x6x16", 0.0, 0.09)])
 def test_cg_fp64_matches_lu(name, ms, sigma):
     need_gpu()
     w = W.workload(name)
@@ -38,7 +38,7 @@ def test_cg_fp64_matches_lu(name, ms, sigma):
 
 def test_cg_initial_guess_and_zero_rhs():
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     ol = OLat.from_params(w.lat)
     with ctx_for(w.lat) as ctx:
         phi, b = dev(w.phi), dev(w.b)
@@ -51,14 +51,14 @@ def test_cg_initial_guess_and_zero_rhs():
 
 def test_spcg_fp32():
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     ol = OLat.from_params(w.lat)
     with ctx_for(w.lat) as ctx:
         x, info = ctx.solve_spcg(dev(w.phi), 0.2, dev(w.b.astype(np.complex64)), tol=1e-5)
     assert true_rel(ol, w.phi, 0.2, 0.0, host(x).astype(np.complex128), w.b.astype(np.complex64)) < 2e-5
 
 
-@pytest.mark.parametrize("name,ms", [("C1", 0.0), ("C3", 0.0), ("C3", 0.5)])
+@pytest.mark.parametrize("name,ms", [("L6x6x16", 0.0), ("L36x36x64", 0.0), ("L36x36x64", 0.5)])
 def test_fgmres_mixed_true_residual(name, ms):
     need_gpu()
     w = W.workload(name)
@@ -79,7 +79,7 @@ def test_fgmres_iteration_structure_matches_oracle():
     may be repeated on the other: restarts agree within one, Arnoldi steps and
     inner iterations closely."""
     need_gpu()
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     ol = OLat.from_params(w.lat)
     A64 = lambda v: of.apply_MMdag(ol, w.phi, 0.0, v)
     A32 = lambda v: of.apply_MMdag(ol, w.phi, 0.0, v.astype(np.complex64)).astype(np.complex64)
@@ -110,7 +110,7 @@ def test_fgmres_fp64_inner_and_no_preconditioning():
 def test_not_converged_is_reported():
     need_gpu()
     import paper_1804_07195_gb300 as hmc
-    w = W.workload("C1")
+    w = W.workload("L6x6x16")
     with ctx_for(w.lat) as ctx:
         with pytest.raises(hmc.HMCError) as e:
             ctx.solve_cg(dev(w.phi), 0.0, dev(w.b), tol=1e-10, maxit=5)
@@ -119,7 +119,7 @@ def test_not_converged_is_reported():
         assert info["iters"] == 5 and info["true_rel_res"] > 1e-10
 
 
-@pytest.mark.parametrize("name,ms", [("C1", 0.0), ("C3", 0.2)])
+@pytest.mark.parametrize("name,ms", [("L6x6x16", 0.0), ("L36x36x64", 0.2)])
 def test_fcg_mixed(name, ms):
     """Flexible CG with the FP32 CG preconditioner (Section 3) against the
     oracle's flexible CG: both converge, in a similar number of outer steps, and
@@ -131,7 +131,7 @@ def test_fcg_mixed(name, ms):
         x, info = ctx.solve_fcg(dev(w.phi), ms, dev(w.b), tol=1e-10)
     assert true_rel(ol, w.phi, ms, 0.0, host(x), w.b) <= 2e-10
     assert info["iters_inner"] > 0
-    if name == "C1":
+    if name == "L6x6x16":
         A64 = lambda v: of.apply_MMdag(ol, w.phi, ms, v)
         A32 = lambda v: of.apply_MMdag(ol, w.phi, ms, v.astype(np.complex64)).astype(np.complex64)
         ref = osv.fcg(A64, A32, w.b, tol=1e-10)
@@ -142,8 +142,8 @@ def test_fcg_mixed(name, ms):
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
-@pytest.mark.parametrize("name,ms,sigma,bound", [("C3", 0.0, 0.0, 1e-3), ("C3", 0.4, 0.05, 5e-5),
-                                                 ("C5", 0.1, 0.0, 1e-3)])
+@pytest.mark.parametrize("name,ms,sigma,bound", [("L36x36x64", 0.0, 0.0, 1e-3), ("L36x36x64", 0.4, 0.05, 5e-5),
+                                                 ("L102x102x64", 0.1, 0.0, 1e-3)])
 def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching,
     persistent) solve

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_tuner_end_to_end():
     need_gpu()
     from paper_1804_07195_gb300 import tuner
-    w = W.workload("C2")
+    w = W.workload("L12x12x32")
     with ctx_for(w.lat) as ctx:
         res = tuner.measure_and_tune(ctx, dev(w.phi), [dev(r) for r in w.rho], repeats=2)
     assert 0 < res.lam_min < res.lam_max

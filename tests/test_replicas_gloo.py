@@ -30,7 +30,7 @@ def _rank_main(rank, world, port, out):
     import bench
     import workloads as W
     ms, work = bench.aggregate_over_ranks(10.0 * (rank + 1), 100.0 + rank, dist)
-    g = W.rng(bench.replica_seed(W.SEEDS["C5"], rank, 0))
+    g = W.rng(bench.replica_seed(W.SEEDS["L102x102x64"], rank, 0))
     first = float(g.normal())
     gathered = [None] * world
     dist.all_gather_object(gathered, first)

@@ -56,7 +56,7 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     import paper_1804_07195_gb300 as hmc
     from paper_1804_07195_gb300 import _abi
     lib = hmc.library()
-    p = W.C5  # 1,331,712 sites > HMC_NOALLOC_MAX_SITES
+    p = W.L102  # 1,331,712 sites > HMC_NOALLOC_MAX_SITES
     assert p.nsites > _abi.HMC_NOALLOC_MAX_SITES
     phi = torch.zeros(p.nsites, dtype=torch.float64, device="cuda")
     x = torch.zeros(p.nsites, dtype=torch.complex128, device="cuda")

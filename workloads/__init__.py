@@ -87,52 +87,54 @@ def make_workload(name: str, lat: LatticeParams, seed, masses: Sequence[float] =
     return Workload(name, lat, phi, b, pi, rho, list(masses))
 
 
-# The five workloads: plain FP64 method on 6x6; Hasenbusch force on 12x12;
-# mixed-precision solve on 36x36; a batch of uneven lattices; one trajectory
-# on the 102x102, nt=64 graphene sheet.
-C1 = LatticeParams(6, 6, 16, kappa=1.0, U=2.0, beta=4.0)
-C2 = LatticeParams(12, 12, 32, kappa=1.0, U=3.0, beta=6.0)
-C3 = LatticeParams(36, 36, 64, kappa=1.0, U=3.5, beta=8.0)
-C5 = LatticeParams(102, 102, 64, kappa=1.0, U=3.8, beta=12.0)
+# The workloads: plain FP64 method on 6x6 (nt 16); Hasenbusch force on 12x12
+# (nt 32); mixed-precision solve on 36x36 (nt 64); a batch of 48 uneven
+# lattices; one trajectory on the 102x102, nt=64 graphene sheet.
+L6 = LatticeParams(6, 6, 16, kappa=1.0, U=2.0, beta=4.0)
+L12 = LatticeParams(12, 12, 32, kappa=1.0, U=3.0, beta=6.0)
+L36 = LatticeParams(36, 36, 64, kappa=1.0, U=3.5, beta=8.0)
+L102 = LatticeParams(102, 102, 64, kappa=1.0, U=3.8, beta=12.0)
 
-C2_MASSES = (0.3, 1.0)
-C4_MASSES = (0.1, 0.5, 2.0)
-C5_MASSES = (0.1, 0.5, 2.0)
-C5_NMD = 30
-C5_NI = (6, 2, 2)
+L12_MASSES = (0.3, 1.0)
+BATCH_MASSES = (0.1, 0.5, 2.0)
+L102_MASSES = (0.1, 0.5, 2.0)
+L102_NMD = 30
+L102_NI = (6, 2, 2)
 OMELYAN_ZETA = 0.193
 
-SEEDS = {"C1": 1001, "C2": 1002, "C3": 1003, "C4": 1004, "C5": 1005}
+SEEDS = {"L6x6x16": 1001, "L12x12x32": 1002, "L36x36x64": 1003, "batch48": 1004, "L102x102x64": 1005}
 
 
 def workload(name: str) -> Workload:
-    if name == "C1":
-        return make_workload("C1", C1, SEEDS["C1"], ())
-    if name == "C2":
-        return make_workload("C2", C2, SEEDS["C2"], C2_MASSES)
-    if name == "C3":
-        return make_workload("C3", C3, SEEDS["C3"], ())
-    if name == "C5":
-        return make_workload("C5", C5, SEEDS["C5"], C5_MASSES)
+    """One of the named workloads: "L6x6x16", "L12x12x32" (two Hasenbusch
+    masses), "L36x36x64", "L102x102x64" (three masses)."""
+    if name == "L6x6x16":
+        return make_workload(name, L6, SEEDS[name], ())
+    if name == "L12x12x32":
+        return make_workload(name, L12, SEEDS[name], L12_MASSES)
+    if name == "L36x36x64":
+        return make_workload(name, L36, SEEDS[name], ())
+    if name == "L102x102x64":
+        return make_workload(name, L102, SEEDS[name], L102_MASSES)
     raise KeyError(name)
 
 
-C4_L = (6, 12, 18, 24, 36)
-C4_NT = (16, 32, 48)
+BATCH_L = (6, 12, 18, 24, 36)
+BATCH_NT = (16, 32, 48)
 
 
-def c4_instances(count: int = 48) -> List[Workload]:
+def batch_instances(count: int = 48) -> List[Workload]:
     """The batched workload: `count` independent instances, lattice size L and
     nt drawn per instance, U=3, beta=6, each carrying one b per shift mass."""
     out = []
-    for k, child in enumerate(np.random.SeedSequence(SEEDS["C4"]).spawn(count)):
+    for k, child in enumerate(np.random.SeedSequence(SEEDS["batch48"]).spawn(count)):
         g = rng(child)
-        L = int(g.choice(C4_L))
-        nt = int(g.choice(C4_NT))
+        L = int(g.choice(BATCH_L))
+        nt = int(g.choice(BATCH_NT))
         lat = LatticeParams(L, L, nt, kappa=1.0, U=3.0, beta=6.0)
         phi = draw_phi(g, lat)
-        bs = [draw_complex(g, lat.nsites) for _ in C4_MASSES]
-        out.append(Workload(f"C4[{k}]", lat, phi, bs[0], np.zeros(0), bs, list(C4_MASSES)))
+        bs = [draw_complex(g, lat.nsites) for _ in BATCH_MASSES]
+        out.append(Workload(f"batch[{k}]", lat, phi, bs[0], np.zeros(0), bs, list(BATCH_MASSES)))
     return out
 
 

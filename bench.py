@@ -170,7 +170,7 @@ def main():
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -544,6 +544,21 @@ def kernel_case(case):
     from paper_1804_07195_gb300 import build
     import workloads as W
     build.build()
+    if case == "mmdag32_stream":
+        # 306x306x64 (12M sites): vectors far larger than L2, L2 flushed before each application
+        lat = hmc.Lattice(306, 306, 64, 1.0, 3.8, 12.0)
+        g = W.rng(9306)
+        phi = torch.tensor(g.normal(0.0, math.sqrt(lat.delta * 3.8), lat.nsites), device="cuda")
+        x = torch.randn(lat.nsites, dtype=torch.complex64, device="cuda")
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        with hmc.Context(lat) as ctx:
+            ctx.load_field(phi)
+            for _ in range(8):
+                flush.zero_()
+                ctx.apply_MMdag(None, 0.1, x)
+            torch.cuda.synchronize()
+        print(json.dumps({"case": case, "sites": lat.nsites, "applications": 8}))
+        return
     if case == "batched":
         sys_ = []
         for w in W.batch_instances():

@@ -25,7 +25,7 @@ from typing import Callable, Dict, List, Sequence, Tuple
 import numpy as np
 
 # Step 2 of Section 7.2: the mass pairs (m_0, m_1) measured with N_0 = N_1 = 1.
-PAPER_MASS_PAIRS = ((0.05, 0.2), (0.1, 0.3), (0.2, 1.5), (0.4, 0.8), (1.2, 2.0))
+SECTION_7_2_MASS_PAIRS = ((0.05, 0.2), (0.1, 0.3), (0.2, 1.5), (0.4, 0.8), (1.2, 2.0))
 
 
 def solver_time_model(ms, t0, lam_max, lam_min):
@@ -150,7 +150,7 @@ def force_norm(g) -> float:
 
 
 def measure_and_tune(ctx, phi, rho, solve_masses: Sequence[float] = (0.05, 0.1, 0.2, 0.4, 0.8, 1.5, 3.0),
-                     pairs: Sequence[Tuple[float, float]] = PAPER_MASS_PAIRS, tol: float = 1e-10,
+                     pairs: Sequence[Tuple[float, float]] = SECTION_7_2_MASS_PAIRS, tol: float = 1e-10,
                      repeats: int = 2) -> TuneResult:
     """Steps 2-4 of Section 7.2 on the field phi (a CUDA tensor) with heat-bath
     vectors rho (three complex128 CUDA tensors): time the mixed-precision

@@ -169,6 +169,11 @@ def main():
                     help="inner tolerance factor a of Algorithm A.1 for the trajectory's solves "
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
+    ap.add_argument("--cg-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="FP32 CG design of the trajectory's context: 0 = autotuned (default); 1-4 pin "
+                         "grid-stride, tiled, marching or persistent (hmc_set_cg_variant). Under a "
+                         "profiler the autotuner's timings are distorted, so launch lists pin the design "
+                         "the tuner chooses without one.")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
@@ -219,6 +224,8 @@ def main():
                   for pi, rho in host_inputs[: args.warmup + args.steps + 1]]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = hmc.Context(lat)
+    if args.cg_variant:
+        ctx.set_cg_variant(args.cg_variant)
     stream = torch.cuda.current_stream()
 
     def trajectory(k, phi_t, pi_t, rho_t):

@@ -410,6 +410,9 @@ def main():
                 "config": {"workload": WORKLOAD + "; " + WORKLOAD_A.format(a=args.fgmres_a),
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "sites": N, "mmdag_applies_per_step": applies / args.steps,
+                           "cg_graph_mode": {2: "device-side loop, one graph launch per solve",
+                                             1: "graph chunks with host checks",
+                                             0: "direct launches"}[ctx.graph_mode()],
                            "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -296,6 +296,13 @@ hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
  * limit_cycles = 0 restore normal operation. */
 hmc_status hmc_set_wait_test(hmc_ctx* ctx, int extra, long long limit_cycles);
 
+/* How the context runs CG iterations: 2 = each solve is one CUDA-graph launch
+ * whose device-side while loop repeats captured chunks of iterations until
+ * the solve is done (the host waits once); 1 = captured chunks replayed with
+ * host checks in between (used when the loop graph cannot be built);
+ * 0 = kernels launched one by one (per-kernel timing on, or no graphs). */
+hmc_status hmc_graph_mode(hmc_ctx* ctx, int* mode);
+
 /* ---- instrumentation ------------------------------------------------------- */
 
 #define HMC_NKERNELS 32

@@ -294,6 +294,13 @@ class Context:
         3: marching; 4: persistent (one cooperative launch per solve)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
+    def graph_mode(self) -> int:
+        """2: one graph launch per CG solve (device-side loop); 1: captured
+        chunks with host checks; 0: kernels launched one by one."""
+        m = C.c_int()
+        self._check(self.lib.hmc_graph_mode(self.h, C.byref(m)))
+        return m.value
+
     def set_wait_test(self, extra: int, limit_cycles: int = 0):
         """Test hook: grid barriers of the persistent FP32 CG kernel wait for
         `extra` more arrivals than there are blocks and give up after

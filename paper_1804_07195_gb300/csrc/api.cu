@@ -113,6 +113,58 @@ hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cu
   return st;
 }
 
+hmc_status capture_loop_graph(hmc_ctx* c, const std::function<hmc_status(cudaGraphConditionalHandle)>& body,
+                              cudaGraphExec_t* out) {
+  *out = nullptr;
+  if (!c->cap_stream) HMC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(c, e, "cudaGraphCreate");
+  }
+  cudaGraphConditionalHandle h{};
+  cudaGraph_t body_graph = nullptr;
+  e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p);
+    if (e == cudaSuccess) body_graph = p.conditional.phGraph_out[0];
+  }
+  hmc_status st = HMC_OK;
+  if (e != cudaSuccess) {
+    st = cuda_fail(c, e, "conditional graph node");
+  } else {
+    cudaStream_t saved = c->stream;
+    c->stream = c->cap_stream;
+    c->capturing = true;
+    c->pdl_armed = false;
+    e = cudaStreamBeginCaptureToGraph(c->cap_stream, body_graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    st = e == cudaSuccess ? body(h) : cuda_fail(c, e, "cudaStreamBeginCaptureToGraph");
+    if (e == cudaSuccess) {
+      cudaGraph_t captured = nullptr;  // the body graph itself, owned by the node
+      cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
+      if (e2 != cudaSuccess && st == HMC_OK) st = cuda_fail(c, e2, "cudaStreamEndCapture");
+    }
+    c->capturing = false;
+    c->pdl_armed = false;
+    c->stream = saved;
+  }
+  if (st == HMC_OK) {
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  cudaGraphDestroy(graph);
+  if (st != HMC_OK) cudaGetLastError();  // a failed capture leaves no error behind
+  return st;
+}
+
 GraphEntry* find_graph(hmc_ctx* c, int kind, const void* const key[6]) {
   for (auto& g : c->graphs) {
     if (g.kind != kind) continue;
@@ -241,6 +293,8 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   if ((e = cudaMemset(c->tickets, 0, sizeof(unsigned) * kTickets)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->sc, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->gbar, sizeof(GridBar))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->loop_trips, 2 * sizeof(unsigned))) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->loop_trips_host, 2 * sizeof(unsigned))) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->gbar, 0, sizeof(GridBar))) != cudaSuccess) return bail(e);
   if ((e = cudaMemset(c->sc, 0, sizeof(CGScal) * 4)) != cudaSuccess) return bail(e);
   // one-item grids of the tuned kernels may reach nsm * 128 blocks of 128 threads
@@ -267,6 +321,8 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   if (c->tickets) cudaFree(c->tickets);
   if (c->sc) cudaFree(c->sc);
   if (c->gbar) cudaFree(c->gbar);
+  if (c->loop_trips) cudaFree(c->loop_trips);
+  if (c->loop_trips_host) cudaFreeHost(c->loop_trips_host);
   for (int i = 0; i < hmc_ctx::kBatchSlots; ++i)
     if (c->bpool[i]) cudaFree(c->bpool[i]);
   for (int i = 0; i < 4; ++i)
@@ -437,6 +493,12 @@ hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   c->tuned32 = false;
   c->persist32 = false;
   destroy_graphs(c);
+  return HMC_OK;
+}
+
+hmc_status hmc_graph_mode(hmc_ctx* c, int* mode) {
+  if (!c || !mode) return HMC_ERR_INVALID;
+  *mode = (!c->use_graphs || c->prof.timing) ? 0 : (c->use_loop_graphs ? 2 : 1);
   return HMC_OK;
 }
 

@@ -147,6 +147,9 @@ struct hmc_ctx {
   long long bar_limit = 0;   // test hook: barrier wait limit in SM cycles (0: default)
 
   bool use_graphs = true;
+  bool use_loop_graphs = true;   // whole solves as one graph with a device-side while loop
+  unsigned* loop_trips = nullptr;       // device: [0] trips of the loop so far, [1] bound
+  unsigned* loop_trips_host = nullptr;  // pinned mirror
   bool capturing = false;
   bool pdl_armed = false;  // a kernel precedes the next launch in the capture
   cudaStream_t cap_stream = nullptr;
@@ -253,6 +256,11 @@ inline hmc_status launch(hmc_ctx* c, int id, F&& f) {
 // Capture the kernels `body` launches into a graph (on cap_stream) and return
 // the instantiated executable; the context's stream is restored afterwards.
 hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cudaGraphExec_t* out);
+// A graph whose single node is a while loop: `body(handle)` is captured as the
+// loop body and must end with a launch that sets the loop condition through
+// `handle` (loop_continue_launch); the body repeats while that value is 1.
+hmc_status capture_loop_graph(hmc_ctx* c, const std::function<hmc_status(cudaGraphConditionalHandle)>& body,
+                              cudaGraphExec_t* out);
 // Cached executable for (kind, key) or NULL.
 GraphEntry* find_graph(hmc_ctx* c, int kind, const void* const key[6]);
 GraphEntry* add_graph(hmc_ctx* c, int kind, const void* const key[6], cudaGraphExec_t exec);

@@ -1500,6 +1500,23 @@ INST(float)
 INST(double)
 #undef INST
 
+// Condition of the device-side CG loop: continue while the solve runs and the
+// trip count is below its bound (trips[1], so the loop ends even if the done
+// flag were never set).
+__global__ void k_loop_continue(cudaGraphConditionalHandle h, const CGScal* sc, unsigned* trips) {
+  if (threadIdx.x == 0) {
+    const unsigned t = trips[0] + 1u;
+    trips[0] = t;
+    cudaGraphSetConditional(h, (sc->done == CG_RUNNING && t < trips[1]) ? 1u : 0u);
+  }
+}
+
+hmc_status loop_continue_launch(hmc_ctx* c, cudaGraphConditionalHandle h, const CGScal* sc) {
+  k_loop_continue<<<1, 32, 0, c->stream>>>(h, sc, c->loop_trips);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HMC_OK : cuda_fail(c, e, "loop condition");
+}
+
 // Tiled variants are usable when the shared-memory window holds the tile's
 // spatial neighbourhood and the grid's reduction partials fit their buffers.
 bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt) {

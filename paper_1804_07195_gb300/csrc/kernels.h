@@ -62,6 +62,9 @@ bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt);
 // (or the residual kernel) left in sc, x, r and p0 (p1: second direction
 // buffer, u: scratch).
 bool cg32_persist_ok(const hmc_ctx* c, const Geo& g);
+// The last launch of a CG loop body: sets the loop condition (sc still
+// running and fewer trips than loop_trips[1]) and counts the trip.
+hmc_status loop_continue_launch(hmc_ctx* c, cudaGraphConditionalHandle h, const CGScal* sc);
 hmc_status cg32_persist_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1,
                                float2* u, CGScal* sc);
 

@@ -236,8 +236,50 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
       c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
     }
   }
+  const int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64,
+                      K_CG_P64};
+  const double kbytes[3] = {sizeof(R) == 4 ? 36.0 : 48.0, sizeof(R) == 4 ? 52.0 : 112.0, 48.0};
+  const int nk = sizeof(R) == 4 ? 2 : 3;
+  // The whole solve as one graph launch: chunks of kChunk iterations repeated
+  // by a device-side while loop until the done flag is set (or the trip bound,
+  // maxit / kChunk + 2, is reached); the host waits once, at the end.
+  bool looped = false;
+  if (!persistent && c->use_graphs && c->use_loop_graphs && !c->prof.timing && !c->capturing) {
+    const void* key[6] = {sc, r, p, q, u, x};
+    const int kind = (sizeof(R) == 4 ? 32 : 64) + 1000;
+    GraphEntry* le = find_graph(c, kind, key);
+    if (!le) {
+      cudaGraphExec_t exec;
+      if (capture_loop_graph(c, [&](cudaGraphConditionalHandle h) -> hmc_status {
+            HMC_TRY(iterate(kChunk));
+            return loop_continue_launch(c, h, sc);
+          }, &exec) == HMC_OK) {
+        le = add_graph(c, kind, key, exec);
+      } else {
+        c->use_loop_graphs = false;  // chunked replay from now on
+        c->err.clear();
+      }
+    }
+    if (le) {
+      c->loop_trips_host[0] = 0u;
+      c->loop_trips_host[1] = (unsigned)(maxit / kChunk + 2);
+      HMC_CUDA(c, cudaMemcpyAsync(c->loop_trips, c->loop_trips_host, 2 * sizeof(unsigned), cudaMemcpyHostToDevice,
+                                  c->stream));
+      HMC_CUDA(c, cudaGraphLaunch(le->exec, c->stream));
+      HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
+      HMC_CUDA(c, cudaMemcpyAsync(c->loop_trips_host, c->loop_trips, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                  c->stream));
+      HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+      const double its = (double)c->loop_trips_host[0] * kChunk;
+      for (int k = 0; k < nk; ++k) {
+        c->prof.launches[kid[k]] += (long long)its;
+        c->prof.bytes[kid[k]] += its * kbytes[k] * g.N;
+      }
+      looped = true;
+    }
+  }
   GraphEntry* ge = nullptr;
-  if (!persistent && c->use_graphs && !c->prof.timing) {
+  if (!persistent && !looped && c->use_graphs && !c->prof.timing) {
     const void* key[6] = {sc, r, p, q, u, x};
     const int kind = sizeof(R) == 4 ? 32 : 64;
     ge = find_graph(c, kind, key);
@@ -251,13 +293,9 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
       }
     }
   }
-  const int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64,
-                      K_CG_P64};
-  const double kbytes[3] = {sizeof(R) == 4 ? 36.0 : 48.0, sizeof(R) == 4 ? 52.0 : 112.0, 48.0};
-  const int nk = sizeof(R) == 4 ? 2 : 3;
   int per_check = 1, checks = 0;
   long long launched = 0;
-  for (; !persistent;) {
+  for (; !persistent && !looped;) {
     for (int i = 0; i < per_check; ++i) {
       if (ge) {
         HMC_CUDA(c, cudaGraphLaunch(ge->exec, c->stream));

@@ -167,3 +167,17 @@ def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     assert info["iters"] > 0 and info["status"] == 0
     assert true_rel(ol, w.phi, ms, sigma, host(x32).astype(np.complex128), b32) < bound
     assert true_rel(ol, w.phi, ms, sigma, host(x), w.b) <= 1e-10
+
+
+def test_solves_run_as_one_graph_launch_with_a_device_loop():
+    """After a solve the context reports the device-side loop graph (one graph
+    launch per CG solve), and a second solve through the cached loop graph gives
+    the same result bit for bit (FP64 CG is deterministic)."""
+    need_gpu()
+    w = W.workload("L6x6x16")
+    with ctx_for(w.lat) as ctx:
+        x1, i1 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
+        assert ctx.graph_mode() == 2
+        x2, i2 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
+    assert i1["iters"] == i2["iters"]
+    assert np.array_equal(host(x1), host(x2))

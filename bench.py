@@ -266,6 +266,7 @@ def main():
         dH.append(H1 - H0)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    graph_mode = ctx.graph_mode()
     clk = clocks.stop()
     if dist is not None:
         dist.barrier()
@@ -412,7 +413,7 @@ def main():
                            "sites": N, "mmdag_applies_per_step": applies / args.steps,
                            "cg_graph_mode": {2: "device-side loop, one graph launch per solve",
                                              1: "graph chunks with host checks",
-                                             0: "direct launches"}[ctx.graph_mode()],
+                                             0: "direct launches"}[graph_mode],
                            "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,

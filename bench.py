@@ -174,6 +174,9 @@ def main():
                          "grid-stride, tiled, marching or persistent (hmc_set_cg_variant). Under a "
                          "profiler the autotuner's timings are distorted, so launch lists pin the design "
                          "the tuner chooses without one.")
+    ap.add_argument("--graph-mode", type=int, default=2, choices=[1, 2],
+                    help="2 = each CG solve one graph launch with a device-side loop (default); 1 = graph "
+                         "chunks with host checks, the mode kernel profilers can see into")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
@@ -181,7 +184,7 @@ def main():
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.kernel_case:
-        kernel_case(args.kernel_case)
+        kernel_case(args.kernel_case, args.graph_mode)
         return
 
     if args.impl == "reference":
@@ -226,6 +229,7 @@ def main():
     ctx = hmc.Context(lat)
     if args.cg_variant:
         ctx.set_cg_variant(args.cg_variant)
+    ctx.set_graph_mode(args.graph_mode)
     stream = torch.cuda.current_stream()
 
     def trajectory(k, phi_t, pi_t, rho_t):
@@ -551,7 +555,7 @@ def aggregate_over_ranks(ms, work, dist, device=None):
     return float(t.item()), float(w.item())
 
 
-def kernel_case(case):
+def kernel_case(case, graph_mode=2):
     """One solve (or 20 operator applications) on the 102x102x64 lattice: the
     case the ncu kernel profiles are taken on."""
     import torch
@@ -594,6 +598,7 @@ def kernel_case(case):
     phi = torch.tensor(w.phi, device="cuda")
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
+        ctx.set_graph_mode(graph_mode)
         if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist"):
             ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
                                 "spcg_persist": 4}[case])

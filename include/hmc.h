@@ -302,6 +302,10 @@ hmc_status hmc_set_wait_test(hmc_ctx* ctx, int extra, long long limit_cycles);
  * host checks in between (used when the loop graph cannot be built);
  * 0 = kernels launched one by one (per-kernel timing on, or no graphs). */
 hmc_status hmc_graph_mode(hmc_ctx* ctx, int* mode);
+/* Choose it: 2 (default) or 1. Profilers that replay single kernels cannot see
+ * kernels inside a graph with a conditional node, so kernel profiles of the
+ * CG iterations are taken in mode 1 (the same kernels, replayed in chunks). */
+hmc_status hmc_set_graph_mode(hmc_ctx* ctx, int mode);
 
 /* ---- instrumentation ------------------------------------------------------- */
 

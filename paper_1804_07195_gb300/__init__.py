@@ -301,6 +301,11 @@ class Context:
         self._check(self.lib.hmc_graph_mode(self.h, C.byref(m)))
         return m.value
 
+    def set_graph_mode(self, mode: int):
+        """2: device-side loop graphs (default); 1: chunks with host checks
+        (kernel profilers see the kernels only in this mode)."""
+        self._check(self.lib.hmc_set_graph_mode(self.h, mode))
+
     def set_wait_test(self, extra: int, limit_cycles: int = 0):
         """Test hook: grid barriers of the persistent FP32 CG kernel wait for
         `extra` more arrivals than there are blocks and give up after

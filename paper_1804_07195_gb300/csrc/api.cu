@@ -502,6 +502,13 @@ hmc_status hmc_graph_mode(hmc_ctx* c, int* mode) {
   return HMC_OK;
 }
 
+hmc_status hmc_set_graph_mode(hmc_ctx* c, int mode) {
+  if (!c) return HMC_ERR_INVALID;
+  if (mode != 1 && mode != 2) return fail(c, HMC_ERR_INVALID, "graph mode must be 1 or 2");
+  c->use_loop_graphs = (mode == 2);
+  return HMC_OK;
+}
+
 hmc_status hmc_set_wait_test(hmc_ctx* c, int extra, long long limit_cycles) {
   if (!c) return HMC_ERR_INVALID;
   if (extra < 0 || limit_cycles < 0) return fail(c, HMC_ERR_INVALID, "extra and limit_cycles must be >= 0");

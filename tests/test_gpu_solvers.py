@@ -179,5 +179,8 @@ def test_solves_run_as_one_graph_launch_with_a_device_loop():
         x1, i1 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
         assert ctx.graph_mode() == 2
         x2, i2 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
-    assert i1["iters"] == i2["iters"]
-    assert np.array_equal(host(x1), host(x2))
+        ctx.set_graph_mode(1)  # chunks with host checks: the same iterations
+        assert ctx.graph_mode() == 1
+        x3, i3 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
+    assert i1["iters"] == i2["iters"] == i3["iters"]
+    assert np.array_equal(host(x1), host(x2)) and np.array_equal(host(x1), host(x3))

@@ -57,6 +57,12 @@ bool cg32_tiled_ok(const hmc_ctx* c, const Geo& g, int tc, int tt);
 // Whether the marching FP32 CG kernels' reduction partials fit their buffers
 // at `threads` cells and `tt` time slices per block.
 bool cg32_march_ok(const hmc_ctx* c, const Geo& g, int threads, int tt);
+// Launch (no instrumentation) of the tiled or marching kernels of the pair
+// for the shape sh; GB / GA: the other kernel's partial count.
+void cg32_alt_pmdag(hmc_ctx* c, const Geo& g, const Shape& sh, const float2* r, const float2* pold, float2* pnew,
+                    float2* u, CGScal* sc, int GB);
+void cg32_alt_m(hmc_ctx* c, const Geo& g, const Shape& sh, const float2* u, const float2* p, float2* x, float2* r,
+                CGScal* sc, int GA);
 // The persistent FP32 CG kernel: whether its on-chip state fits this lattice,
 // and one cooperative launch that runs the whole solve from the state k_init0
 // (or the residual kernel) left in sc, x, r and p0 (p1: second direction

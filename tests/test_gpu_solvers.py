@@ -143,16 +143,19 @@ def test_fcg_mixed(name, ms):
 
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("name,ms,sigma,bound", [("L36x36x64", 0.0, 0.0, 1e-3), ("L36x36x64", 0.4, 0.05, 5e-5),
-                                                 ("L102x102x64", 0.1, 0.0, 1e-3)])
+                                                 ("L102x102x64", 0.1, 0.0, 1e-3), ("L36x36x21", 0.2, 0.0, 1e-4)])
 def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching,
     persistent) solve
     to the single-precision floor, and FGMRES built on them meets 1e-10. The
     FP32 solution's true residual is bounded by the recursive tolerance plus
     the rounding drift, about eps_32 times the condition number (near 10^4 at
-    m_s = 0 on a 64-slice lattice, where lambda_min = 4 sin^2(pi / 128))."""
+    m_s = 0 on a 64-slice lattice, where lambda_min = 4 sin^2(pi / 128)). The
+    21-slice lattice leaves a ragged last block of time slices for every slice
+    count per block the tiled and marching kernels can take (2, 4, 8), and a
+    ragged last block of cells."""
     need_gpu()
-    w = W.workload(name)
+    w = W.small(36, 36, 21, seed=2121, U=3.0, beta=6.0) if name == "L36x36x21" else W.workload(name)
     ol = OLat.from_params(w.lat)
     with ctx_for(w.lat) as ctx:
         ctx.set_cg_variant(variant)

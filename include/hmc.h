@@ -269,7 +269,11 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
                              const hmc_solver_opts* action_opts, double* H0, double* H1,
                              hmc_solve_info* agg);
 
-/* ---- launch shapes ---------------------------------------------------------- */
+/* ---- launch shapes and graphs ----------------------------------------------- */
+
+/* The calls of this section and the next choose or report how the library
+ * runs the paper's operations on the GPU; they have no counterpart in the
+ * paper and change no result beyond floating-point rounding order. */
 
 /* The CG kernels' launch shapes are chosen by an autotuner on a context's first
  * solve in each precision (timed candidates; see hmc_profile_read for the

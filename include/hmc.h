@@ -273,7 +273,8 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
 
 /* The calls of this section and the next choose or report how the library
  * runs the paper's operations on the GPU; they have no counterpart in the
- * paper and change no result beyond floating-point rounding order. */
+ * paper and, apart from the wait test hook, change no result beyond the
+ * rounding order of floating-point sums. */
 
 /* The CG kernels' launch shapes are chosen by an autotuner on a context's first
  * solve in each precision (timed candidates; see hmc_profile_read for the

@@ -625,13 +625,19 @@ def kernel_case(case, graph_mode=2):
     print(json.dumps({"case": case, **{k: v for k, v in info.items()}}))
 
 
+# the translation unit of the FP32 CG pair (the kernels whose DRAM traffic
+# profiles/traffic.json records): kernels.cu and everything it includes
+PAIR_SOURCES = ("paper_1804_07195_gb300/csrc/kernels.cu", "paper_1804_07195_gb300/csrc/kernels.h",
+                "paper_1804_07195_gb300/csrc/ctx.h", "paper_1804_07195_gb300/csrc/common.cuh",
+                "paper_1804_07195_gb300/csrc/operator.cuh", "paper_1804_07195_gb300/csrc/launch.cuh",
+                "include/hmc.h")
+
+
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1804_07195_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in PAIR_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -304,6 +304,17 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
   }
 }
 
+// Condition of the batched device-side loop: continue while fewer than
+// `target` systems have finished and the trip count is below trips[1].
+__global__ void kb_loop_continue(cudaGraphConditionalHandle h, const unsigned* ndone, unsigned target,
+                                 unsigned* trips) {
+  if (threadIdx.x == 0) {
+    const unsigned t = trips[0] + 1u;
+    trips[0] = t;
+    cudaGraphSetConditional(h, (*ndone < target && t < trips[1]) ? 1u : 0u);
+  }
+}
+
 // FP64 u = M^dagger x for every system (plain)
 __global__ void __launch_bounds__(512) kb_mdag64(const BSys* __restrict__ sys, const int* __restrict__ bsys,
                                                  const double2* __restrict__ E, const double2* __restrict__ x,
@@ -547,6 +558,43 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   for (int i = 0; i < w.nsys; ++i) pre_done += w.st_host[i].cg.done != CG_RUNNING;
   if (pre_done == w.nsys) return HMC_OK;
   const int chunk = 8;
+  const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
+  const double bytes_iter = sizeof(R) == 8 ? 192.0 : 88.0;
+  // One graph launch for the whole batched solve: a device-side while loop
+  // repeats the captured chunk until every running system is done (counted
+  // in ndone) or the trip bound maxit / chunk + 2 is reached.
+  if (c->use_loop_graphs && !c->prof.timing) {
+    const unsigned target = (unsigned)(w.nsys - pre_done);
+    cudaGraphExec_t lexec = nullptr;
+    const hmc_status cs = capture_loop_graph(c, [&](cudaGraphConditionalHandle h) -> hmc_status {
+      for (int i = 0; i < chunk; ++i) cg_iteration<R>(w, c->stream, x, r, p, q, u, i);
+      kb_loop_continue<<<1, 32, 0, c->stream>>>(h, w.ndone, target, c->loop_trips);
+      const cudaError_t e2 = cudaGetLastError();
+      return e2 == cudaSuccess ? HMC_OK : cuda_fail(c, e2, "batched loop condition");
+    }, &lexec);
+    if (cs == HMC_OK) {
+      c->loop_trips_host[0] = 0u;
+      c->loop_trips_host[1] = (unsigned)(maxit / chunk + 2);
+      cudaError_t e = cudaMemcpyAsync(c->loop_trips, c->loop_trips_host, 2 * sizeof(unsigned),
+                                      cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaGraphLaunch(lexec, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->loop_trips_host, c->loop_trips, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaGraphExecDestroy(lexec);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched loop graph");
+      const long long launched = (long long)c->loop_trips_host[0] * chunk;
+      double bytes = 0.0;
+      for (int i = 0; i < w.nsys; ++i) bytes += (double)w.st_host[i].cg.iter * w.hsys[i].g.N * bytes_iter;
+      c->prof.bytes[kid] += bytes;
+      c->prof.launches[kid] += 2 * launched;
+      *iters_launched += launched;
+      (void)nactive;
+      return HMC_OK;
+    }
+    c->err.clear();  // fall back to the chunked loop below
+  }
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   HMC_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -559,8 +607,6 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   }
   hmc_status status = HMC_OK;
   long long launched = 0;
-  const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
-  const double bytes_iter = sizeof(R) == 8 ? 192.0 : 88.0;
   std::vector<char> running(w.nsys);
   for (int i = 0; i < w.nsys; ++i) running[i] = w.st_host[i].cg.done == CG_RUNNING;
   // the host reads the states after 1, 1, 2, 4, 4, ... chunks

@@ -6,8 +6,10 @@ import pytest
 import scipy.linalg as sla
 
 import workloads as W
-from oracle import action, fermion, integrators
+from oracle import action, integrators
 from oracle.lattice import Lattice
+
+from exact_ensemble import blocked, phi2_exact
 
 
 def harmonic_map(step_fn, h):
@@ -154,29 +156,8 @@ def test_hmc_samples_the_exact_distribution():
         if it >= 100:
             meas.append(phi @ phi)
             expdh.append(np.exp(-dH))
-    meas = np.array(meas)
-    blocks = meas[: len(meas) // 50 * 50].reshape(-1, 50).mean(axis=1)
-    hmc, hmc_err = blocks.mean(), blocks.std(ddof=1) / np.sqrt(len(blocks))
-    eb = np.array(expdh)[: len(expdh) // 50 * 50].reshape(-1, 50).mean(axis=1)
-    assert abs(eb.mean() - 1.0) < 5 * eb.std(ddof=1) / np.sqrt(len(eb)) + 1e-3
-    # exact expectation by reweighting Gaussian samples with det(M M^dagger)
-    ns = 200000
-    ph = g.normal(0.0, np.sqrt(lat.delta * lat.U), size=(ns, lat.N))
-    M0 = fermion.dense_M(lat, np.zeros(lat.N), 0.0)
-    tp, _ = lat.time_partner()
-    rows = np.arange(lat.N)
-    Ms = np.repeat(M0[None], ns, axis=0)
-    hops = np.stack([fermion.time_hop(lat, p, 0.0) for p in ph[:2000]])  # check helper
-    Ms[:, rows, tp] = 0.0
-    s, _, _, _ = lat.coords()
-    _, sign = lat.time_partner()
-    Ms[:, rows, tp] = sign * np.where(s == 0, np.exp(1j * ph), -np.exp(-1j * ph))
-    assert np.allclose(Ms[:2000, rows, tp], hops)
-    _, ld = np.linalg.slogdet(Ms)
-    wts = np.exp(2 * ld - (2 * ld).max())
-    obs = (ph * ph).sum(axis=1)
-    exact = (wts * obs).sum() / wts.sum()
-    # importance-sampling error by the delta method
-    wn = wts / wts.sum()
-    ex_err = np.sqrt(((wn * (obs - exact)) ** 2).sum())
+    hmc, hmc_err = blocked(meas)
+    eb, eb_err = blocked(expdh)
+    assert abs(eb - 1.0) < 5 * eb_err + 1e-3
+    exact, ex_err = phi2_exact(lat, g)
     assert abs(hmc - exact) < 4 * np.hypot(hmc_err, ex_err), (hmc, hmc_err, exact, ex_err)

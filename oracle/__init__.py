@@ -14,6 +14,8 @@ stated beside the code.
 Modules:
   lattice     -- honeycomb torus, neighbour and time-shift tables (Section 2)
   fermion     -- M, M^dagger, M M^dagger, dense M, free-field spectrum (Eq. ferm_op)
+  free_field  -- M M^dagger + sigma applied and inverted exactly by FFT for a
+                 constant field (Eq. ferm_op in plane waves)
   solvers     -- dense LU, CG, single-precision CG, flexible GMRES (Algorithm A.1)
   action      -- log det, pseudofermion action and force, Hasenbusch terms
                  (Eqs. hamiltonian, p_dot, eta_xi, f_chi_i, def_xi_i)

@@ -137,3 +137,47 @@ def test_force_at_full_size_is_the_action_derivative():
             Sm, _ = ctx.action(phi - h * dd, masses, chis, opts=opts)
             fd = (Sp - Sm) / (2 * h)
             assert abs(fd - an) <= 1e-6 * abs(an) + 40 * eps * abs(S0) / h, (fd, an, S0)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_full_size_force_against_closed_form_solves(method):
+    """102x102x64 with the three Hasenbusch masses and a constant field
+    phi = 0.3, where every solve has the exact free-field form: the oracle's own
+    pseudofermions, action and force (Sections 5.1, Eqs. f_chi_i, def_xi_i),
+    computed with those exact solves, against the library's, with solves at
+    1e-13 (FP64 CG and mixed FGMRES). The heat-bath vectors are random, so the
+    force varies from site to site. Each solution is within kappa * 1e-13
+    (kappa about 2300 here) of the exact one in norm; the pseudofermions and
+    the force, linear and bilinear in the solutions, get a few times that, and
+    1e-8 leaves a margin above it. The actions, a sum of 1.3M terms, agree to
+    1e-11 relative."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    from oracle import free_field
+    w = W.workload("L102x102x64")
+    ol = OLat.from_params(w.lat)
+    theta = 0.3
+    masses = list(w.masses)
+    phi = np.full(ol.N, theta)
+
+    def exact_solve(p, ms, b):
+        assert np.all(p == theta)
+        return free_field.solve_A(ol, ms, 0.0, b, theta)
+
+    kappa = max(free_field.condition_number(ol, mu, 0.0, theta) for mu in [0.0] + masses)
+    assert kappa < 3000
+    chis = oa.make_chi(ol, phi, masses, list(w.rho), exact_solve)
+    F_ref = oa.total_grad(ol, phi, masses, chis, exact_solve)
+    S_ref = oa.total_action(ol, phi, masses, chis, exact_solve)
+    opts = hmc.SolverOpts(method=method, tol=1e-13, maxit=200000)
+    with ctx_for(w.lat) as ctx:
+        phid = dev(phi)
+        gchis, _ = ctx.make_chi(phid, masses, [dev(r) for r in w.rho], opts=opts)
+        F, _ = ctx.force(phid, masses, [dev(c) for c in chis], opts=opts)
+        S, _ = ctx.action(phid, masses, [dev(c) for c in chis], opts=opts)
+    for g, c in zip(gchis, chis):
+        assert np.linalg.norm(host(g) - c) <= 1e-8 * np.linalg.norm(c)
+    F = host(F)
+    assert np.linalg.norm(F - F_ref) <= 1e-8 * np.linalg.norm(F_ref)
+    assert rel_max(F, F_ref) <= 1e-8
+    assert abs(S - S_ref) <= 1e-11 * abs(S_ref), (S, S_ref)

@@ -127,6 +127,21 @@ def cpu_oracle_apply(seconds: float):
     return lat.N * reps / dt / 1e9, reps, dt
 
 
+def cpu_oracle_cg(iters: int):
+    """The oracle's FP64 CG (the same algorithm as the library's FP64 CG) on
+    the same lattice and m_s = 0 system, stopped after `iters` iterations:
+    milliseconds per iteration."""
+    import workloads as W
+    from oracle import fermion, solvers
+    from oracle.lattice import Lattice
+    w = W.workload("L102x102x64")
+    lat = Lattice.from_params(w.lat)
+    t0 = time.perf_counter()
+    res = solvers.cg(lambda v: fermion.apply_MMdag(lat, w.phi, 0.0, v), w.b, tol=1e-10, maxit=iters)
+    dt = time.perf_counter() - t0
+    return 1e3 * dt / max(res.iters, 1), res.iters
+
+
 def run_reference(args, rank):
     """Reference arm: the CPU oracle (numpy, complex128) as it stands, each step
     a bounded sample of the same workload: oracle M M^dagger applications on
@@ -415,6 +430,14 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"numpy complex128 oracle M M^dagger on the same 1,331,712-site lattice, "
                          f"{reps} applications in {dt:.1f} s (single-threaded numpy)"}
+        cg_ms, cg_it = cpu_oracle_cg(6)
+        gpu_cg = solve["fp64_cg"]
+        cpu["cg"] = {"iterations_timed": cg_it, "ms_per_iteration": cg_ms,
+                     "fp64_cg_solve_estimate_s": cg_ms * gpu_cg["iters"] / 1e3,
+                     "note": f"the oracle's FP64 CG on the m_s = 0 system of this lattice; the solve estimate "
+                             f"is its time per iteration times the {gpu_cg['iters']} iterations the GPU's FP64 "
+                             f"CG takes to 1e-10 (same algorithm), against {gpu_cg['ms']:.1f} ms FP64 and "
+                             f"{solve['mixed_fgmres']['ms']:.1f} ms mixed on the GPU"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -43,21 +43,23 @@ def slice_indices(n: int, m: int, nt: int, t: int) -> np.ndarray:
 
 
 def correlator(ctx, lat, phi, orbital: np.ndarray, t0s: Sequence[int], tol: float = 1e-12) -> np.ndarray:
-    """C(tau) on one configuration, averaged over the source slices t0s."""
+    """C(tau) on one configuration, averaged over the source slices t0s. The
+    vectors live on phi's device (the GPU: the context's solves run there)."""
     import torch
     n, m, nt = lat.n, lat.m, lat.nt
     N = lat.nsites
-    o = torch.tensor(orbital, device="cuda")
-    out = torch.zeros(nt, dtype=torch.complex128, device="cuda")
+    dev = phi.device
+    o = torch.tensor(orbital, device=dev)
+    out = torch.zeros(nt, dtype=torch.complex128, device=dev)
     ctx.load_field(phi)
-    idx = torch.tensor(np.stack([slice_indices(n, m, nt, t) for t in range(nt)]), device="cuda")  # (nt, 2V)
+    idx = torch.tensor(np.stack([slice_indices(n, m, nt, t) for t in range(nt)]), device=dev)  # (nt, 2V)
     for t0 in t0s:
-        b = torch.zeros(N, dtype=torch.complex128, device="cuda")
+        b = torch.zeros(N, dtype=torch.complex128, device=dev)
         b[idx[t0]] = o
         y, _ = ctx.solve_cg(None, 0.0, b, tol=tol)
         col = ctx.apply_Mdag(None, 0.0, y)
         per_t = col[idx] @ o.conj()                 # projection on every slice t
-        tau = torch.arange(nt, device="cuda")
+        tau = torch.arange(nt, device=dev)
         t = (t0 + tau) % nt
         sign = torch.where(t0 + tau >= nt, -1.0, 1.0).to(torch.complex128)
         out += sign * per_t[t]

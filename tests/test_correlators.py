@@ -64,7 +64,7 @@ class DenseOracleContext:
         return torch.tensor(fermion.apply_Mdag(self.lat, self.phi, ms, x.numpy()))
 
 
-@pytest.mark.parametrize("k1,t0s", [(0.0, [0, 3]), (np.pi, [1, 5, 6])])
+@pytest.mark.parametrize("k1,t0s", [(0.0, [0, 3]), (np.pi, [1, 5, 6]), (None, [2, 7])])
 def test_correlator_assembly_on_a_random_field(k1, t0s):
     """correlator() against a plain loop over the dense propagator M^{-1} on a
     random field: the source sits on slice t0, every sink slice is projected on
@@ -75,7 +75,11 @@ def test_correlator_assembly_on_a_random_field(k1, t0s):
     w = W.small(2, 1, 8, seed=81, U=4.0, beta=8.0)
     lat = Lattice.from_params(w.lat)
     G = np.linalg.inv(fermion.dense_M(lat, w.phi, 0.0))
-    o = cr.band_orbital(lat.n, lat.m, k1)
+    if k1 is None:  # any complex source vector on a slice (the band orbitals here are real)
+        g = np.random.default_rng(7)
+        o = g.normal(size=2 * lat.V) + 1j * g.normal(size=2 * lat.V)
+    else:
+        o = cr.band_orbital(lat.n, lat.m, k1)
     ref = np.zeros(lat.nt, complex)
     for t0 in t0s:
         col = G[:, cr.slice_indices(lat.n, lat.m, lat.nt, t0)] @ o

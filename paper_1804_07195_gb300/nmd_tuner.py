@@ -12,6 +12,9 @@ The tuner alternates two phases until one of its stopping rules holds:
 It stops after 500 trajectories in all, when the proposed N_MD has already
 been measured three times, or when the target fell inside the measured
 confidence interval three times.
+An experiment can be saved (`save_history`) and resumed from its
+measurements (`tune_nmd(..., resume=load_history(path))`), the algorithm's
+"initialise or resume" step.
 
 The skew-normal CDF (Azzalini's distribution) is Phi(x) - 2 T(x, alpha) with
 T Owen's T function. This module is host logic only: `simulate(nmd)` runs one
@@ -20,8 +23,9 @@ trajectory's acceptance probability min(1, exp(-dH)).
 """
 from __future__ import annotations
 
+import json
 import math
-from dataclasses import dataclass, field
+from dataclasses import asdict, dataclass, field
 from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -125,19 +129,47 @@ class NmdTuneResult:
     params: Optional[Tuple[float, float, float]] = None
 
 
+def save_history(history: Sequence[NmdMeasurement], path: str) -> None:
+    """Write the measurements of an experiment (one entry per N_MD phase) as
+    JSON, for a later run to resume from."""
+    with open(path, "w") as f:
+        json.dump({"history": [asdict(h) for h in history]}, f)
+
+
+def load_history(path: str) -> List[NmdMeasurement]:
+    with open(path) as f:
+        return [NmdMeasurement(**h) for h in json.load(f)["history"]]
+
+
 def tune_nmd(simulate: Callable[[int], float], nmd0: int = 500, target: float = TARGET_ACCEPTANCE,
              ci_width: float = 0.25, min_trajectories: int = 5, max_total: int = 500,
-             repeat_stop: int = 3, hit_stop: int = 3, multiple: int = 1, z: float = 1.96) -> NmdTuneResult:
+             repeat_stop: int = 3, hit_stop: int = 3, multiple: int = 1, z: float = 1.96,
+             resume: Optional[Sequence[NmdMeasurement]] = None) -> NmdTuneResult:
     """Algorithm B.1. `simulate(nmd)` runs one trajectory with N_MD = nmd and
     returns its acceptance probability; `multiple` rounds every proposed N_MD
-    up to a multiple of the coarsest time-scale ratio."""
+    up to a multiple of the coarsest time-scale ratio.
+
+    `resume`: the measurements of a previous experiment (the algorithm's
+    "initialise or resume" step). They count as if just made: the model is fitted
+    to them, the stopping rules see them, and their trajectories count toward
+    `max_total`; the run then continues at the N_MD the model proposes, so an
+    experiment split at a phase boundary ends as the unsplit one would."""
     nmd = int(math.ceil(nmd0 / multiple) * multiple)
-    nmd_list: List[int] = []
-    p_list: List[float] = []
-    history: List[NmdMeasurement] = []
-    total = 0
-    hits = 0
+    history: List[NmdMeasurement] = list(resume or [])
+    nmd_list: List[int] = [h.nmd for h in history]
+    p_list: List[float] = [h.mean for h in history]
+    total = sum(h.trajectories for h in history)
+    hits = sum(1 for h in history if h.lower <= target <= h.upper)
     params = None
+    if history:
+        params = fit_acceptance(nmd_list, p_list)
+        nmd = predict_nmd(params, target, multiple)
+        if total >= max_total:
+            return NmdTuneResult(nmd, "trajectory limit", total, history, params)
+        if nmd_list.count(nmd) >= repeat_stop:
+            return NmdTuneResult(nmd, "repeated N_MD", total, history, params)
+        if hits >= hit_stop:
+            return NmdTuneResult(nmd, "target inside interval", total, history, params)
     while True:
         # phase 1: measure the acceptance at nmd until its interval is narrow
         samples: List[float] = []

@@ -119,3 +119,38 @@ def test_tuner_stops_at_the_trajectory_limit():
 def test_tuner_respects_time_scale_multiple():
     res = nt.tune_nmd(gaussian_hmc(2.0e5, 7), nmd0=500, multiple=4)
     assert all(h.nmd % 4 == 0 for h in res.history) and res.nmd % 4 == 0
+
+
+@pytest.mark.parametrize("C,seed,split", [(2.0e5, 3, 1), (3.0e7, 4, 2)])
+def test_resumed_experiment_ends_as_the_unsplit_one(tmp_path, C, seed, split):
+    """Algorithm B.1 resumed from a saved experiment: stopping after `split`
+    phases (trajectory limit at that phase's end), saving the measurements,
+    loading them and resuming with the same trajectory stream reproduces the
+    unsplit run: the same N_MD, stopping rule, trajectory count and phases."""
+    full = nt.tune_nmd(gaussian_hmc(C, seed), nmd0=500)
+    assert len(full.history) > split
+    sim = gaussian_hmc(C, seed)
+    first = nt.tune_nmd(sim, nmd0=500, max_total=sum(h.trajectories for h in full.history[:split]))
+    assert first.reason == "trajectory limit" and len(first.history) == split
+    path = str(tmp_path / "nmd.json")
+    nt.save_history(first.history, path)
+    resumed = nt.tune_nmd(sim, nmd0=500, resume=nt.load_history(path))
+    assert (resumed.nmd, resumed.reason, resumed.total_trajectories) == \
+        (full.nmd, full.reason, full.total_trajectories)
+    assert [(h.nmd, h.trajectories, h.mean) for h in resumed.history] == \
+        [(h.nmd, h.trajectories, h.mean) for h in full.history]
+
+
+def test_resume_applies_the_stopping_rules_first():
+    """A resumed experiment that already meets a stopping rule runs no
+    trajectory."""
+    def never(nmd):
+        raise AssertionError("no trajectory expected")
+
+    hit = [nt.NmdMeasurement(40, 0.66, 0.6, 0.72, 10)] * 3
+    res = nt.tune_nmd(never, resume=hit)
+    assert res.reason in ("target inside interval", "repeated N_MD") and res.total_trajectories == 30
+    spent = [nt.NmdMeasurement(20, 0.1, 0.0, 0.3, 250), nt.NmdMeasurement(60, 0.9, 0.8, 1.0, 250)]
+    res = nt.tune_nmd(never, resume=spent)
+    assert res.reason == "trajectory limit" and res.total_trajectories == 500
+    assert 20 < res.nmd < 60

@@ -94,3 +94,41 @@ def test_run_chain_thermalises_and_measures_on_its_cadence():
     # every trajectory is accepted and adds 1: measurements after trajectories 6, 9, ..., 24
     assert res.measurements == seen == [6.0 + 3 * k for k in range(7)]
     assert res.dH == [-1.0] * 20
+
+
+class MomentumContext(FakeContext):
+    """A 'trajectory' that depends on the draws: phi moves by 0.1 pi and dH is
+    pi[0] (so the Metropolis decisions vary); it reports solver statistics."""
+
+    def md_trajectory(self, phi, pi, masses, rhos, integ, md_opts, action_opts):
+        phi.add_(0.1 * pi + 0.01 * rhos[0].real)
+        return 1.0, 1.0 + float(pi[0]), {"iters": 7, "true_rel_res": 1e-11}
+
+
+def test_checkpoint_resume_continues_the_chain_exactly(tmp_path):
+    N, masses = 16, [0.3]
+    full = chain.Chain(MomentumContext(N, 0.0), zeros(N), masses, None, None, seed=99)
+    dh_full = [full.trajectory(None)[0] for _ in range(12)]
+    part = chain.Chain(MomentumContext(N, 0.0), zeros(N), masses, None, None, seed=99)
+    dh = [part.trajectory(None)[0] for _ in range(5)]
+    path = str(tmp_path / "chain.npz")
+    part.save(path)
+    resumed = chain.Chain.load(MomentumContext(N, 0.0), path, None, None, device="cpu")
+    assert resumed.masses == masses and resumed.trajectories == 5
+    dh += [resumed.trajectory(None)[0] for _ in range(7)]
+    assert dh == dh_full
+    assert torch.equal(resumed.phi, full.phi)
+    assert resumed.trajectories == full.trajectories == 12 and resumed.accepted == full.accepted
+    assert 0 < full.accepted < 12
+
+
+def test_run_log_has_one_json_line_per_trajectory(tmp_path):
+    import json
+    path = str(tmp_path / "run.jsonl")
+    ch = chain.Chain(MomentumContext(8, 0.0), zeros(8), [], None, None, seed=4, log=path)
+    out = [ch.trajectory(None) for _ in range(6)]
+    lines = [json.loads(s) for s in open(path).read().splitlines()]
+    assert [r["trajectory"] for r in lines] == list(range(1, 7))
+    assert [r["dH"] for r in lines] == [d for d, _ in out]
+    assert [r["accepted"] for r in lines] == [bool(a) for _, a in out]
+    assert all(r["H1"] - r["H0"] == r["dH"] and r["solver"]["iters"] == 7 for r in lines)

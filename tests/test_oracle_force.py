@@ -93,6 +93,24 @@ def test_hasenbusch_equal_masses_give_zero_force():
     assert np.abs(action.term_grad(lat, phi1, masses, chis, 0, solve)).max() > 1e-3
 
 
+def test_hasenbusch_force_is_linear_in_the_mass_gap():
+    """For nearly equal neighbouring masses the term's force grows in
+    proportion to mu_1 - mu_0 (Section 7.2: the small force of the Hasenbusch
+    tuner): doubling a small gap doubles the force, to first order."""
+    w, lat, solve = setup(masses=(0.4, 0.4))
+    phi1 = w.phi + 0.1 * np.random.default_rng(2).normal(size=lat.N)
+
+    def force(eps):
+        masses = (0.4, 0.4 + eps)
+        chis = action.make_chi(lat, w.phi, masses, w.rho, solve)
+        return action.term_grad(lat, phi1, masses, chis, 1, solve)
+
+    f1, f2 = force(1e-3), force(2e-3)
+    assert np.linalg.norm(f1) > 1e-6
+    assert abs(np.linalg.norm(f2) / np.linalg.norm(f1) - 2.0) < 1e-2
+    assert np.linalg.norm(f2 - 2 * f1) < 1e-2 * np.linalg.norm(f2)
+
+
 @pytest.mark.parametrize("i", [0, 1, 2])
 def test_hasenbusch_term_force_vs_finite_differences(i):
     masses = (0.3, 1.0)

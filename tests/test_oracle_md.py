@@ -161,3 +161,29 @@ def test_hmc_samples_the_exact_distribution():
     assert abs(eb - 1.0) < 5 * eb_err + 1e-3
     exact, ex_err = phi2_exact(lat, g)
     assert abs(hmc - exact) < 4 * np.hypot(hmc_err, ex_err), (hmc, hmc_err, exact, ex_err)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape,seed", [((2, 1, 8), 9), ((3, 3, 4), 10)])
+def test_mean_exp_minus_dH_is_one(shape, seed):
+    """<exp(-dH)> = 1 over an equilibrium chain (reversible, area-preserving
+    MD; Section 2) on the 2x1 and 3x3 tori with one Hasenbusch mass. The step
+    size (N_MD = 4, <dH> about 0.08) keeps exp(-dH) well behaved: near the
+    integrator's stability limit its distribution is so heavy-tailed that the
+    sample mean converges far more slowly than its standard error suggests."""
+    lat = Lattice(*shape, 1.0, 2.0, 2.0)
+    solve = action.SolveA(lat, "dense")
+    g = np.random.default_rng(seed)
+    phi = np.zeros(lat.N)
+    ex = []
+    for it in range(2100):
+        pi = g.normal(size=lat.N)
+        rhos = [(g.normal(size=lat.N) + 1j * g.normal(size=lat.N)) * np.sqrt(0.5) for _ in range(2)]
+        p1, _, H0, H1, _ = integrators.trajectory(lat, phi, pi, rhos, (0.5,), 4, (2,), solve)
+        dH = H1 - H0
+        if g.uniform() < np.exp(-dH):
+            phi = p1
+        if it >= 100:
+            ex.append(np.exp(-dH))
+    mean, err = blocked(ex, 100)
+    assert abs(mean - 1.0) < 4 * err + 1e-3, (mean, err)

@@ -62,3 +62,36 @@ def test_product_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", src), f
+
+
+@pytest.mark.parametrize("params", [
+    (4096, 4096, 32, 1.0, 2.0, 4.0),          # exactly 2^30 sites: above the index range
+    (1 << 20, 1 << 20, 1 << 20, 1.0, 2.0, 4.0),  # n*m*nt overflows 32 bits
+    (3, 3, 8, float("nan"), 2.0, 4.0),
+    (3, 3, 8, 1.0, float("inf"), 4.0),
+    (3, 3, 8, 1.0, 2.0, 0.0),
+    (3, 3, 8, 1.0, 0.0, 4.0),                 # U = 0: the Gaussian term 1/(delta U) is undefined
+    (3, 3, 8, 1.0, -1.0, 4.0),
+    (3, -1, 8, 1.0, 2.0, 4.0),
+])
+def test_invalid_lattices_are_rejected_before_any_cuda_call(lib, params):
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    h = ctypes.c_void_p()
+    lat = _abi.hmc_lattice(*params)
+    assert L.hmc_create(ctypes.byref(h), ctypes.byref(lat), None) == _abi.HMC_ERR_INVALID
+    assert not h.value
+
+
+def test_largest_accepted_lattice_passes_validation(lib):
+    """2 * 4096 * 4096 * 31 sites (just under 2^30) passes the size check: without
+    a GPU the create call then fails in CUDA, not as an invalid argument."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("would allocate tens of GB on the device")
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    h = ctypes.c_void_p()
+    lat = _abi.hmc_lattice(4096, 4096, 31, 1.0, 2.0, 4.0)
+    assert L.hmc_create(ctypes.byref(h), ctypes.byref(lat), None) in (_abi.HMC_ERR_CUDA, _abi.HMC_ERR_NOMEM)
+    assert not h.value

@@ -95,3 +95,14 @@ def test_largest_accepted_lattice_passes_validation(lib):
     lat = _abi.hmc_lattice(4096, 4096, 31, 1.0, 2.0, 4.0)
     assert L.hmc_create(ctypes.byref(h), ctypes.byref(lat), None) in (_abi.HMC_ERR_CUDA, _abi.HMC_ERR_NOMEM)
     assert not h.value
+
+
+def test_every_status_has_its_own_message(lib):
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    codes = [_abi.HMC_OK, _abi.HMC_ERR_INVALID, _abi.HMC_ERR_CUDA, _abi.HMC_ERR_NOT_CONVERGED,
+             _abi.HMC_ERR_NAN, _abi.HMC_ERR_TIMEOUT, _abi.HMC_ERR_NOMEM]
+    msgs = [L.hmc_status_string(c) for c in codes]
+    assert all(m and m != b"unknown status" for m in msgs) and len(set(msgs)) == len(codes)
+    assert L.hmc_status_string(-99) == b"unknown status"
+    assert L.hmc_last_error(None) == b""

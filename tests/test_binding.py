@@ -30,3 +30,11 @@ def test_no_context_without_a_gpu():
     with pytest.raises((RuntimeError, ValueError)):
         hmc.apply_MMdag_noalloc(hmc.Lattice(3, 3, 8, 1.0, 2.0, 4.0), torch.zeros(144, dtype=torch.float64), 0.0,
                                 torch.zeros(144, dtype=torch.complex128))
+
+
+def test_missing_library_raises(tmp_path, monkeypatch):
+    """Without the built libhmc.so the package raises; nothing else computes."""
+    from paper_1804_07195_gb300 import _abi
+    monkeypatch.setattr(_abi, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _abi.load(str(tmp_path / "libhmc.so"))

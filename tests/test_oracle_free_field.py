@@ -89,3 +89,18 @@ def test_cg_at_36x36x64_reaches_the_exact_solution():
     rel_res = np.linalg.norm(free_field.apply_A(lat, ms, sigma, res.x, theta) - b) / np.linalg.norm(b)
     assert res.converged and rel_res <= 1.01e-10
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= kappa * rel_res
+
+
+def test_spectral_edge_at_the_papers_setting(paper):
+    """At the setting of the paper's solver-time fit (N_t = 256, beta kappa = 8,
+    m_s = 0) the free-field upper edge 4 cos^2(pi / 2 nt) + 9 (delta kappa)^2
+    (omega nearest pi, k = 0, the same on any torus) lies inside the fitted
+    lambda_max = 4.1 +- 0.2 of Section 6.1. The fit was made on interacting
+    configurations of a nanotube, so this is a consistency check of the
+    operator's scale, not a sharp pin."""
+    lat = Lattice(3, 3, 256, 1.0, 3.5, 8.0)
+    lam = free_field.mode_eigenvalues(lat, 0.0)
+    dk = lat.delta * lat.kappa
+    edge = 4 * np.cos(np.pi / 512) ** 2 + 9 * dk * dk
+    assert abs(lam.max() - edge) < 1e-12
+    assert abs(edge - paper["solver_time_fit"]["lambda_max"]) <= 0.2

@@ -23,21 +23,24 @@ from .lattice import A, Lattice
 
 
 def dM_dphi(lat: Lattice, phi: np.ndarray) -> np.ndarray:
-    """The one nonzero entry of dM/dphi_{x,t}, per row (x,t)."""
+    """The one nonzero entry of dM/dphi_{x,t}, per row (x,t). Eq. ferm_op; the derivative entering Eqs. p_dot
+    and f_chi_i."""
     s, _, _, _ = lat.coords()
     _, sign = lat.time_partner()
     return sign * np.where(s == A, 1j * np.exp(1j * phi), 1j * np.exp(-1j * phi))
 
 
 def logdet_MMdag(lat: Lattice, phi: np.ndarray, ms: float = 0.0) -> float:
-    """log det(M M^dagger) = 2 log|det M|, by dense LU (numpy slogdet)."""
+    """log det(M M^dagger) = 2 log|det M|, by dense LU (numpy slogdet). The fermion weight det(M M^dagger) of
+    Eq. hamiltonian."""
     _, ld = np.linalg.slogdet(fermion.dense_M(lat, phi, ms))
     return 2.0 * float(ld)
 
 
 def grad_logdet_MMdag(lat: Lattice, phi: np.ndarray, ms: float = 0.0) -> np.ndarray:
     """d/dphi_{x,t} log det(M M^dagger) = 2 Re tr(M^{-1} dM/dphi_{x,t})
-    = 2 Re( (M^{-1})_{tp(x,t), (x,t)} * dM_{(x,t), tp(x,t)} )."""
+    = 2 Re( (M^{-1})_{tp(x,t), (x,t)} * dM_{(x,t), tp(x,t)} ). Derivative of the fermion weight of Eq.
+    hamiltonian."""
     Minv = np.linalg.inv(fermion.dense_M(lat, phi, ms))
     tp, _ = lat.time_partner()
     rows = np.arange(lat.N)
@@ -111,14 +114,15 @@ def grad_pf_action(lat: Lattice, phi, ms, chi, solve: SolveA) -> np.ndarray:
 #       = (M_{mu_i} chi_i)^dagger (M_{mu_{i-1}} M_{mu_{i-1}}^dagger)^{-1} (M_{mu_i} chi_i), i < n.
 
 def lower_mass(masses: Sequence[float], i: int) -> float:
-    """mu_{i-1}, with mu_{-1} = 0 (the unshifted operator)."""
+    """mu_{i-1}, with mu_{-1} = 0 (the unshifted operator). Section 5.1."""
     return 0.0 if i == 0 else float(masses[i - 1])
 
 
 def make_chi(lat: Lattice, phi, masses: Sequence[float], rhos: Sequence[np.ndarray],
              solve: SolveA) -> List[np.ndarray]:
     """Pseudofermions from heat-bath vectors rho_i:
-    chi_n = M_{mu_{n-1}} rho_n;  chi_i = M_{mu_i}^dagger (M_{mu_i} M_{mu_i}^dagger)^{-1} M_{mu_{i-1}} rho_i."""
+    chi_n = M_{mu_{n-1}} rho_n;  chi_i = M_{mu_i}^dagger (M_{mu_i} M_{mu_i}^dagger)^{-1} M_{mu_{i-1}}
+    rho_i. Section 5.1."""
     n = len(masses)
     if len(rhos) != n + 1:
         raise ValueError("need n+1 heat-bath vectors for n masses")
@@ -133,6 +137,7 @@ def make_chi(lat: Lattice, phi, masses: Sequence[float], rhos: Sequence[np.ndarr
 
 
 def term_action(lat: Lattice, phi, masses, chis, i: int, solve: SolveA) -> float:
+    """S_i of the Hasenbusch splitting with staggered masses (Section 5.1)."""
     n = len(masses)
     lo = lower_mass(masses, i)
     if i == n:
@@ -159,12 +164,13 @@ def term_grad(lat: Lattice, phi, masses, chis, i: int, solve: SolveA) -> np.ndar
 
 
 def total_action(lat: Lattice, phi, masses, chis, solve: SolveA) -> float:
-    """S(phi) = (1/2) phi^2/(delta U) + sum_i S_i."""
+    """S(phi) = (1/2) phi^2/(delta U) + sum_i S_i. Eq. hamiltonian with the splitting of Section 5.1."""
     return gaussian_action(lat, phi) + sum(
         term_action(lat, phi, masses, chis, i, solve) for i in range(len(masses) + 1))
 
 
 def total_grad(lat: Lattice, phi, masses, chis, solve: SolveA) -> np.ndarray:
+    """dS/dphi of total_action: the Gaussian term plus every term (Eqs. p_dot, f_chi_i, def_xi_i)."""
     g = grad_gaussian(lat, phi)
     for i in range(len(masses) + 1):
         g = g + term_grad(lat, phi, masses, chis, i, solve)

@@ -24,7 +24,8 @@ from .lattice import Lattice
 
 def hopping_matrix(lat: Lattice) -> np.ndarray:
     """Spatial hopping matrix K (sites ordered A(i,j) then B(i,j), cell index
-    j*n + i), K_xy = number of bonds between x and y."""
+    j*n + i), K_xy = number of bonds between x and y. Section 8.1's 4-site model, with the neighbour
+    reading of lattice.py."""
     n, m = lat.n, lat.m
     V = n * m
     K = np.zeros((2 * V, 2 * V))
@@ -40,7 +41,7 @@ def hopping_matrix(lat: Lattice) -> np.ndarray:
 
 class Fock:
     """Fermionic Fock space of `nmodes` modes with Jordan-Wigner ordered
-    creation operators as dense matrices (mode = 2*site + spin)."""
+    creation operators as dense matrices (mode = 2*site + spin). Section 8.1 (exact diagonalisation)."""
 
     def __init__(self, nmodes: int):
         self.nmodes = nmodes
@@ -59,6 +60,7 @@ class Fock:
 
 
 def hubbard_hamiltonian(lat: Lattice, fock: Fock) -> np.ndarray:
+    """The Hubbard Hamiltonian of the module docstring on the Fock space (Section 8.1)."""
     K = hopping_matrix(lat)
     ns = K.shape[0]
     H = np.zeros((fock.dim, fock.dim))
@@ -76,7 +78,7 @@ def hubbard_hamiltonian(lat: Lattice, fock: Fock) -> np.ndarray:
 
 def upper_band_orbital(lat: Lattice, k1: float, k2: float = 0.0) -> np.ndarray:
     """Single-particle orbital of the upper free band (energy +kappa |f(k)|) at
-    lattice momentum (k1, k2), as coefficients over the sites of hopping_matrix."""
+    lattice momentum (k1, k2), as coefficients over the sites of hopping_matrix. Section 8.1."""
     n, m = lat.n, lat.m
     V = n * m
     a = np.zeros(2 * V, complex)
@@ -94,7 +96,7 @@ def upper_band_orbital(lat: Lattice, k1: float, k2: float = 0.0) -> np.ndarray:
 
 
 def quasiparticle_energy(lat: Lattice, k1: float, k2: float = 0.0, tol: float = 1e-10) -> float:
-    """E(N+1, k) - E_0(N) for a particle added in the upper band at k."""
+    """E(N+1, k) - E_0(N) for a particle added in the upper band at k. Section 8.1."""
     ns = 2 * lat.n * lat.m
     fock = Fock(2 * ns)
     H = hubbard_hamiltonian(lat, fock)

@@ -21,7 +21,7 @@ from .lattice import A, B, Lattice
 
 def time_hop(lat: Lattice, phi: np.ndarray, ms: float) -> np.ndarray:
     """The time-hopping entry of M in every row (x, t), boundary sign included:
-    A rows: +s (e^{+i phi_{x,t}} - delta m_s), B rows: -s (e^{-i phi_{x,t}} - delta m_s)."""
+    A rows: +s (e^{+i phi_{x,t}} - delta m_s), B rows: -s (e^{-i phi_{x,t}} - delta m_s). Eq. ferm_op."""
     s, _, _, _ = lat.coords()
     _, sign = lat.time_partner()
     dm = lat.delta * ms
@@ -37,7 +37,7 @@ def diagonal(lat: Lattice) -> np.ndarray:
 
 
 def apply_M(lat: Lattice, phi: np.ndarray, ms: float, psi: np.ndarray) -> np.ndarray:
-    """(M psi)(x,t) = d(x) psi(x,t) + hop(x,t) psi(time partner) - delta kappa sum_nb psi."""
+    """(M psi)(x,t) = d(x) psi(x,t) + hop(x,t) psi(time partner) - delta kappa sum_nb psi. Eq. ferm_op."""
     tp, _ = lat.time_partner()
     nb = lat.spatial_neighbours()
     hop = time_hop(lat, phi, ms)
@@ -49,7 +49,7 @@ def apply_M(lat: Lattice, phi: np.ndarray, ms: float, psi: np.ndarray) -> np.nda
 def apply_Mdag(lat: Lattice, phi: np.ndarray, ms: float, psi: np.ndarray) -> np.ndarray:
     """(M^dagger psi)(y) = sum_x conj(M_xy) psi(x): the time entry of row x sits in
     column tp(x); its conjugate moves psi(x) to y = tp(x). The hopping part is
-    real and symmetric, the diagonal real."""
+    real and symmetric, the diagonal real. Eq. ferm_op."""
     tp, _ = lat.time_partner()
     nb = lat.spatial_neighbours()
     hop = time_hop(lat, phi, ms)
@@ -106,7 +106,7 @@ def dense_M(lat: Lattice, phi: np.ndarray, ms: float) -> np.ndarray:
 def sparse_M(lat: Lattice, phi: np.ndarray, ms: float) -> sp.csc_matrix:
     """M as a scipy sparse matrix: per row the diagonal entry, the time-hopping
     entry at its time partner, and -delta kappa at each of the three hopping
-    partners (duplicates summed, as for n or m below 3)."""
+    partners (duplicates summed, as for n or m below 3). Eq. ferm_op."""
     rows = np.arange(lat.N)
     tp, _ = lat.time_partner()
     nb = lat.spatial_neighbours()
@@ -126,7 +126,7 @@ def free_spectrum(lat: Lattice, ms: float, theta: float = 0.0) -> np.ndarray:
     a = -1 + (e^{i theta} - delta m_s) e^{-i omega} and
     |f|^2 = 3 + 2 cos k1 + 2 cos k2 + 2 cos(k1 - k2), so M M^dagger is
     |a|^2 + (delta kappa)^2 |f|^2 times the 2x2 identity in every block.
-    Returns the N eigenvalues, sorted."""
+    Returns the N eigenvalues, sorted. Eq. ferm_op."""
     nt = lat.nt
     omega = (2 * np.arange(nt) + 1) * np.pi / nt
     k1 = 2 * np.pi * np.arange(lat.n) / lat.n

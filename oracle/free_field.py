@@ -26,7 +26,7 @@ def mode_eigenvalues(lat: Lattice, ms: float, sigma: float = 0.0, theta: float =
     """lambda(omega_l, k1, k2) on the grid (nt, m, n) in numpy FFT order along
     each axis: index l along time is omega_l = (2l + 1) pi / nt, index j2 along
     the second cell axis is k2 = 2 pi j2 / m, index j1 along the first is
-    k1 = 2 pi j1 / n."""
+    k1 = 2 pi j1 / n. Eq. ferm_op in plane waves."""
     omega = (2 * np.arange(lat.nt) + 1) * np.pi / lat.nt
     k2 = 2 * np.pi * np.arange(lat.m) / lat.m
     k1 = 2 * np.pi * np.arange(lat.n) / lat.n
@@ -50,17 +50,17 @@ def _multiply(lat: Lattice, v: np.ndarray, factor: np.ndarray) -> np.ndarray:
 
 
 def apply_A(lat: Lattice, ms: float, sigma: float, v: np.ndarray, theta: float = 0.0) -> np.ndarray:
-    """(M M^dagger + sigma) v for phi = theta everywhere."""
+    """(M M^dagger + sigma) v for phi = theta everywhere. Eq. ferm_op in plane waves."""
     return _multiply(lat, v, mode_eigenvalues(lat, ms, sigma, theta))
 
 
 def solve_A(lat: Lattice, ms: float, sigma: float, b: np.ndarray, theta: float = 0.0) -> np.ndarray:
-    """(M M^dagger + sigma)^{-1} b for phi = theta everywhere."""
+    """(M M^dagger + sigma)^{-1} b for phi = theta everywhere. Eq. ferm_op in plane waves."""
     return _multiply(lat, b, 1.0 / mode_eigenvalues(lat, ms, sigma, theta))
 
 
 def condition_number(lat: Lattice, ms: float, sigma: float = 0.0, theta: float = 0.0) -> float:
     """lambda_max / lambda_min of A: the factor by which a relative residual
-    can grow into the relative error of a solution."""
+    can grow into the relative error of a solution. Eq. ferm_op in plane waves."""
     lam = mode_eigenvalues(lat, ms, sigma, theta)
     return float(lam.max() / lam.min())

@@ -32,7 +32,7 @@ from .lattice import Lattice
 
 
 class Phase:
-    """(phi, pi) with a version counter for the force cache."""
+    """(phi, pi) with a version counter for the force cache. Section 2 (the HMC outline)."""
 
     def __init__(self, phi: np.ndarray, pi: np.ndarray):
         self.phi = phi.astype(np.float64).copy()
@@ -55,6 +55,7 @@ class Phase:
 
 
 def leapfrog(st: Phase, grad: Callable, nsteps: int, tau: float = 1.0):
+    """Section 4 (c1 = c2 = 1/2, d1 = 1, d2 = 0)."""
     h = tau / nsteps
     for _ in range(nsteps):
         st.Q(0.5 * h)
@@ -63,6 +64,7 @@ def leapfrog(st: Phase, grad: Callable, nsteps: int, tau: float = 1.0):
 
 
 def omelyan(st: Phase, grad: Callable, nsteps: int, tau: float = 1.0, zeta: float = 0.193):
+    """Section 4.1, force first as in Section 5.2."""
     nested_omelyan(st, grad, [nsteps], tau, zeta)
 
 
@@ -97,7 +99,7 @@ def level_steps(nmd: int, N: Sequence[int]) -> List[int]:
 
 def nested_omelyan(st: Phase, grad: Callable, steps: Sequence[int], tau: float = 1.0,
                    zeta: float = 0.193):
-    """Multi-time-scale Omelyan integrator. steps[k] = steps of level k per trajectory."""
+    """Multi-time-scale Omelyan integrator. steps[k] = steps of level k per trajectory. Section 5.2."""
     L = len(steps)
     ratio = [steps[0]] + [steps[k] // steps[k - 1] for k in range(1, L)]
     for k in range(1, L):

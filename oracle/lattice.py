@@ -20,6 +20,7 @@ B = 1
 
 
 class Lattice:
+    """Section 2 and Eq. ferm_op, with the readings of the module docstring."""
     def __init__(self, n: int, m: int, nt: int, kappa: float, U: float, beta: float):
         if min(n, m, nt) < 1:
             raise ValueError("n, m, nt must be positive")
@@ -32,20 +33,24 @@ class Lattice:
 
     @classmethod
     def from_params(cls, p) -> "Lattice":
+        """Section 2."""
         return cls(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
 
     def index(self, s, t, i, j):
+        """The canonical layout of the module docstring."""
         return ((s * self.nt + t) * self.m + j) * self.n + i
 
     def coords(self):
-        """Arrays (s, t, i, j) for every canonical index, in index order."""
+        """Arrays (s, t, i, j) for every canonical index, in index order. The canonical layout of the module
+        docstring."""
         s, t, j, i = np.meshgrid(np.arange(2), np.arange(self.nt), np.arange(self.m),
                                  np.arange(self.n), indexing="ij")
         return s.ravel(), t.ravel(), i.ravel(), j.ravel()
 
     def spatial_neighbours(self) -> np.ndarray:
         """(N, 3) array: the three hopping partners of every space-time site,
-        at the same time slice, on the other sublattice."""
+        at the same time slice, on the other sublattice. Eq. ferm_op, with the neighbour reading of the
+        module docstring."""
         s, t, i, j = self.coords()
         n, m = self.n, self.m
         nb = np.empty((self.N, 3), dtype=np.int64)

@@ -33,6 +33,7 @@ import scipy.linalg as sla
 
 
 def dense_solve(Amat: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """The plain definition x = A^{-1} b (Section 3)."""
     lu = sla.lu_factor(Amat)
     return sla.lu_solve(lu, b)
 
@@ -43,12 +44,14 @@ def vdot64(u: np.ndarray, v: np.ndarray) -> complex:
 
 
 def norm2_64(u: np.ndarray) -> float:
+    """Section 3."""
     uu = u.astype(np.complex128)
     return float(np.real(np.vdot(uu, uu)))
 
 
 @dataclass
 class SolveResult:
+    """Section 3 and Appendix A."""
     x: np.ndarray
     iters: int
     converged: bool
@@ -249,5 +252,6 @@ def fcg(apply_A: Callable, apply_A32: Callable, b: np.ndarray, tol: float = 1e-1
 
 
 def true_rel_residual(apply_A: Callable, x: np.ndarray, b: np.ndarray) -> float:
+    """Section 3: the true residual, checked in FP64."""
     r = b.astype(np.complex128) - apply_A(x.astype(np.complex128))
     return float(np.sqrt(norm2_64(r) / norm2_64(b)))

@@ -1,6 +1,9 @@
 // The libhmc kernels: operator applications, fused CG iterations (the
 // grid-stride FP32 pair; the other FP32 designs are in cg32_designs.cu),
 // residuals, FGMRES vector operations and the pseudofermion force.
+// Passages: the operator of Eq. ferm_op (Section 2), CG (Section 3), the vector
+// steps of Algorithm A.1 (Appendix A), the force of Eqs. p_dot, f_chi_i and
+// def_xi_i, the energies of Eq. hamiltonian.
 #include "kernels.h"
 #include "launch.cuh"
 #include "operator.cuh"
@@ -45,6 +48,7 @@ const double kKernelBytesPerSite[K_COUNT] = {
     0};  // persistent CG: 56 B per site and iteration, counted after the solve
 
 // ---------------------------------------------------------------------------
+// e^{i phi} for the FP64 stencils of Eq. ferm_op, and phi rounded to float.
 __global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restrict__ phi,
                                                     double2* __restrict__ E,
                                                     float* __restrict__ phi32) {
@@ -58,6 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restr
 }
 
 
+// out = M^dagger p (Eq. ferm_op, conjugate transpose), one cell-time per thread.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_mdag(Geo g, Phase<R> ph, R dm,
                                                    const V2<R>* __restrict__ p,
@@ -70,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_mdag(Geo g, Phase<R> ph, R dm,
   }
 }
 
+// out = M u (Eq. ferm_op), one cell-time per thread.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_m(Geo g, Phase<R> ph, R dm, const V2<R>* __restrict__ u,
                                                 const V2<R>* __restrict__ y, R sigma,
@@ -89,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_m(Geo g, Phase<R> ph, R dm, const 
   }
 }
 
+// FP64 CG (Section 3), first kernel of an iteration:
 // u = M^dagger p; pAp = |u|^2 + sigma |p|^2 = <p, (M M^dagger + sigma) p>; alpha = rr / pAp.
 template <typename R>
 __global__ void __launch_bounds__(kMaxThreads) k_cg_mdag(Geo g, Phase<R> ph,
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_mdag(Geo g, Phase<R> ph,
   }
 }
 
+// FP64 CG (Section 3), second kernel of an iteration:
 // A p = M u + sigma p;  x += alpha p;  r -= alpha A p;  beta = |r_new|^2 / |r|^2.
 template <typename R>
 __global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
@@ -173,6 +181,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_m(Geo g, Phase<R> ph,
   }
 }
 
+// p = r + beta p, the last step of a CG iteration (Section 3).
 template <typename R>
 __global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __restrict__ r,
                                                    V2<R>* __restrict__ p, const CGScal* sc) {
@@ -193,6 +202,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg_p(int N, const V2<R>* __rest
 // kernel sums those partials itself in the same fixed order (so all blocks hold
 // identical scalars) after pdl_wait() has made them visible.
 //
+// The single-precision CG of Section 3 (the inner solver of Algorithm A.1) as
+// a pair of kernels per iteration.
 // Kernel A (iteration i): rr_i = sum of B's partials; convergence and limit
 // checks; beta = rr_i / rr_{i-1} (0 on the first iteration); then
 //   p_new = r + beta p_old, u = M^dagger p_new,
@@ -382,6 +393,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
   ff_write_partial(loc, partB);
 }
 
+// True residual b - (M M^dagger + sigma) x and its norm in FP64 (Section 3;
+// the restart step of Algorithm A.1).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
                                                     const V2<R>* __restrict__ u,
@@ -505,6 +518,7 @@ __global__ void __launch_bounds__(kThreads) k_redot(int N, const double2* __rest
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
+// Arnoldi step of Algorithm A.1 (classical Gram-Schmidt in two passes):
 // h[i] = V_i^H w for the NV basis vectors (NV a compile-time constant, so the
 // basis pointers stay in the parameter bank and every loop unrolls).
 template <int NV>
@@ -556,6 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_gsupd(int N, VecList V, const doub
   if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) *ww = tot[0];
 }
 
+// v_j = w / |w| (Algorithm A.1).
 __global__ void __launch_bounds__(kThreads) k_scale(int N, double s, const double2* __restrict__ w,
                                                     double2* __restrict__ v, float2* __restrict__ v32) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
@@ -567,6 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(int N, double s, const doubl
   }
 }
 
+// x += sum_i y_i z_i, the update of Algorithm A.1 after the least-squares solve.
 __global__ void __launch_bounds__(kThreads) k_xupd(int N, VecList Z, CoefList y, int nz,
                                                    double2* __restrict__ x) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
@@ -580,6 +596,7 @@ __global__ void __launch_bounds__(kThreads) k_xupd(int N, VecList Z, CoefList y,
   }
 }
 
+// The MD updates phi += c dt pi and pi -= d dt F (Sections 2, 4 and 5.2).
 __global__ void __launch_bounds__(kThreads) k_axpy_real(int N, double a, const double* __restrict__ x,
                                                         double* __restrict__ y) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
@@ -594,6 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_axpby_c(int N, double a, const dou
   }
 }
 
+// Pseudofermion force (Eqs. p_dot, f_chi_i, def_xi_i):
 // Force of one term at the cell-time q. dM/dphi in row k is i s e^{+i phi} (A)
 // or i s e^{-i phi} (B), s = -1 on the wrapping hop; its column is the time
 // partner (t-1 for A, t+1 for B). With c = conj(eta_k) dM_k w_tp:
@@ -629,6 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_force(Geo g, Phase<double> ph,
   }
 }
 
+// d/dphi of phi^2 / (2 delta U), the Gaussian term of Eq. hamiltonian.
 __global__ void __launch_bounds__(kThreads) k_gauss_grad(int N, const double* __restrict__ phi,
                                                          double inv_dU, int accumulate,
                                                          double* __restrict__ grad) {
@@ -638,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss_grad(int N, const double* __
   }
 }
 
+// Sums of squares for the kinetic and Gaussian terms of H (Eq. hamiltonian).
 __global__ void __launch_bounds__(kThreads) k_half_sq(int N, const double* __restrict__ a, double sa,
                                                       const double* __restrict__ b, double* out,
                                                       double* partials, unsigned* ticket) {

@@ -1,5 +1,6 @@
 // C ABI entry points of libhmc: context management, argument validation,
-// operator applications, solves and instrumentation.
+// operator applications, solves and instrumentation. The operations and their
+// passages in the paper are listed in include/hmc.h.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

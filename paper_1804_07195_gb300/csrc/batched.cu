@@ -1,5 +1,7 @@
 // Batched solves of many independent systems (M_s M_s^dagger + sigma_s) x_s = b_s,
-// lattices of uneven sizes, in one launch per kernel.
+// lattices of uneven sizes, in one launch per kernel: the CG of Section 3 and
+// the FGMRES of Algorithm A.1 run for every system at once, each with its own
+// operator of Eq. ferm_op (lattice, phases, staggered mass).
 //
 // Layout: the systems' vectors are concatenated; system s occupies sites
 // [off_s, off_s + N_s) in its own canonical order. Every block belongs to one

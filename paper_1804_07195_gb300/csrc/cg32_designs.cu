@@ -1,7 +1,8 @@
 // The three alternative designs of the FP32 CG iteration (the grid-stride
 // pair in kernels.cu is the fourth): shared-memory tiled kernels, marching
 // kernels, and the persistent cooperative kernel. The autotuner times them
-// against the pair (solvers.cu); hmc_set_cg_variant pins one.
+// against the pair (solvers.cu); hmc_set_cg_variant pins one. All of them run
+// the single-precision CG of Section 3 on the operator of Eq. ferm_op.
 #include "kernels.h"
 #include "launch.cuh"
 #include "operator.cuh"

@@ -1,5 +1,6 @@
 // out = (M M^dagger + sigma) in, complex128, for callers that cannot allocate
-// device memory: no context, no cudaMalloc, no library allocation.
+// device memory: no context, no cudaMalloc, no library allocation (the
+// operator of Eq. ferm_op, in FP64).
 //
 // The intermediate M^dagger in lives in a file-scope static device array of
 // HMC_NOALLOC_MAX_SITES complex128 entries (16 MiB), which every GPU that loads

@@ -1,7 +1,9 @@
 """GB300 (sm_103a) Hybrid Monte Carlo hot path for the Hubbard model on the
 honeycomb lattice (arXiv:1804.07195): the fermion operator M[phi] and its
-adjoint, CG and mixed-precision flexible GMRES solves of M M^dagger, the
-Hasenbusch-split pseudofermion force and the multi-time-scale MD trajectory.
+adjoint (Eq. ferm_op), CG and mixed-precision flexible GMRES solves of
+M M^dagger (Section 3, Algorithm A.1), the Hasenbusch-split pseudofermion force
+(Section 5.1, Eqs. p_dot, f_chi_i, def_xi_i) and the multi-time-scale MD
+trajectory (Sections 2, 4 and 5.2).
 
 The compute lives in libhmc.so (C ABI, include/hmc.h). This package is its
 thin binding: `Context` mirrors the hmc_* entry points with the same names

@@ -92,12 +92,21 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        with open(self.path) as f:
+            lines = f.readlines()
+        os.unlink(self.path)
+        return self.summarise(lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the highest maximum clock, the throttle reasons seen
+        active in any sample, and the peak power, from nvidia-smi CSV lines in
+        the order of FIELDS (no header, no units)."""
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
                 rows.append(parts)
-        os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]

@@ -86,6 +86,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            if os.path.exists(self.path):
+                os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:

@@ -49,3 +49,10 @@ def test_stop_reads_the_samples_and_removes_the_file():
     assert out["samples"] == 2 and out["sm_mhz"] == 2070.0 and out["reasons"] == []
     assert not os.path.exists(s.path)
     assert s.proc.poll() is not None
+
+
+def test_unavailable_sampler_leaves_no_file():
+    s = bench.ClockSampler(None)
+    s.proc = None
+    out = s.stop()
+    assert out["reasons"] == ["nvidia-smi unavailable"] and not os.path.exists(s.path)

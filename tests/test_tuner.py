@@ -65,3 +65,69 @@ def test_two_masses_give_nearly_equal_time_scales(paper):
     N0, N1 = tuner.two_mass_time_scales(Np)
     assert N0 == N1 == max(1, math.floor(math.sqrt(Np[0] * Np[1])))
     assert tuner.nmd_for_time_scales(29, (N0, N1)) % N0 == 0
+
+
+class _Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def now(self):
+        return self.t
+
+
+class _ModelContext:
+    """Stands in for a Context in measure_and_tune: a solve at staggered mass
+    m_s advances the clock by Eq. solver_time_eqn, and the chi_1 and top-term
+    forces are constant vectors whose root mean square follows Eqs.
+    small_force_eqn and large_force_eqn."""
+
+    def __init__(self, torch, clock, N, t_par, small, large):
+        self.torch, self.clock, self.N = torch, clock, N
+        self.t_par, self.small, self.large = t_par, small, large
+        self.solves = []
+
+    def load_field(self, phi):
+        pass
+
+    def solve_fgmres(self, phi, ms, b, tol):
+        self.solves.append(ms)
+        self.clock.t += float(tuner.solver_time_model(ms, *self.t_par))
+        return None, {}
+
+    def make_chi(self, phi, masses, rho, opts=None):
+        return list(masses), {}
+
+    def force(self, phi, masses, chis, term, flags, opts=None):
+        m0, m1 = masses
+        v = tuner.small_force_model(m0, m1, *self.small) if term == 1 else tuner.large_force_model(m1, *self.large)
+        return self.torch.full((self.N,), float(v), dtype=self.torch.float64), {}
+
+
+def test_measure_and_tune_recovers_the_models(paper, monkeypatch):
+    """Steps 2-4 of Section 7.2 end to end on model data: the fitted spectral
+    bounds and force models reproduce the ones the data came from, the masses
+    follow Eq. mu_i_eqn and the time scales Eqs. approx_N_i_eqn and used_N_eqn."""
+    torch = pytest.importorskip("torch")
+    clock = _Clock()
+    monkeypatch.setattr(tuner.time, "perf_counter", clock.now)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    lam = paper["solver_time_fit"]
+    sf = paper["small_force_fit"]
+    lf = paper["large_force_fit"]
+    t_par = (0.01, lam["lambda_max"], lam["lambda_min"])
+    small = (sf["a"], sf["b"], sf["c"])
+    large = (3.0, 0.1, lf["b"], lf["c"])
+    N = 64
+    ctx = _ModelContext(torch, clock, N, t_par, small, large)
+    res = tuner.measure_and_tune(ctx, torch.zeros(N, dtype=torch.float64),
+                                 [torch.zeros(N, dtype=torch.complex128)] * 3, repeats=2)
+    assert ctx.solves == [m for m in (0.05, 0.1, 0.2, 0.4, 0.8, 1.5, 3.0) for _ in range(2)]
+    assert math.isclose(res.lam_min, lam["lambda_min"], rel_tol=1e-6)
+    assert math.isclose(res.lam_max, lam["lambda_max"], rel_tol=1e-6)
+    assert np.allclose(res.small_force, small, rtol=1e-5)
+    mu = tuner.hasenbusch_masses(lam["lambda_min"], lam["lambda_max"], 2)
+    assert np.allclose(res.masses, mu, rtol=1e-6)
+    top = [m1 for _, m1 in tuner.SECTION_7_2_MASS_PAIRS] + [mu[1]]
+    assert np.allclose(tuner.large_force_model(top, *res.large_force), tuner.large_force_model(top, *large),
+                       rtol=1e-6)
+    assert res.N == tuner.two_mass_time_scales(tuner.two_mass_ratios(mu, small, large))

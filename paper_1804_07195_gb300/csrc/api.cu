@@ -9,6 +9,7 @@
 #include <string>
 
 #include "solvers.h"
+#include "validate.h"
 
 using namespace hmc;
 
@@ -86,6 +87,21 @@ void prof_end(hmc_ctx* c, int id, cudaEvent_t a) {
   cudaEventRecord(b, c->stream);
   c->prof.pending.push_back(Pending{a, b, id});
   if (c->prof.pending.size() > 16384) prof_drain(c, 8192);
+}
+
+void prof_discard_last(hmc_ctx* c, int id, long long n, double bytes_each) {
+  if (n <= 0) return;
+  c->prof.launches[id] -= n;
+  c->prof.bytes[id] -= bytes_each * (double)n;
+  auto& P = c->prof.pending;
+  long long left = n;
+  for (size_t i = P.size(); i-- > 0 && left > 0;) {
+    if (P[i].id != id) continue;
+    c->prof.free_events.push_back(P[i].a);
+    c->prof.free_events.push_back(P[i].b);
+    P.erase(P.begin() + i);
+    --left;
+  }
 }
 
 hmc_status capture_graph(hmc_ctx* c, const std::function<hmc_status()>& body, cudaGraphExec_t* out) {
@@ -214,16 +230,6 @@ hmc_status prepare_field(hmc_ctx* c, const double* phi) {
 
 }  // namespace hmc
 
-static bool bad_lattice(const hmc_lattice* L) {
-  if (!L) return true;
-  if (L->n < 1 || L->m < 1 || L->nt < 2) return true;
-  const long long N = 2LL * L->n * L->m * L->nt;
-  if (N >= (1LL << 30)) return true;
-  if (!std::isfinite(L->kappa) || !std::isfinite(L->U) || !std::isfinite(L->beta)) return true;
-  if (!(L->beta > 0.0) || !(L->U > 0.0)) return true;
-  return false;
-}
-
 static hmc_status check_vec(hmc_ctx* c, const void* p, int prec, const char* what) {
   if (p == nullptr) return fail(c, HMC_ERR_INVALID, std::string(what) + " is NULL");
   const uintptr_t al = prec == 64 ? 16 : 8;
@@ -236,6 +242,9 @@ static hmc_status check_mass(hmc_ctx* c, double ms) {
   if (1.0 - c->delta * ms == 0.0) return fail(c, HMC_ERR_INVALID, "1 - delta*m_s == 0: the time hop vanishes");
   return HMC_OK;
 }
+
+// Bytes of one complex vector of the context's lattice in precision prec.
+static size_t vec_bytes(const hmc_ctx* c, int prec) { return (size_t)c->geo.N * (prec == 64 ? 16 : 8); }
 
 static hmc_status check_prec(hmc_ctx* c, int prec) {
   if (prec != 32 && prec != 64) return fail(c, HMC_ERR_INVALID, "prec must be 32 or 64");
@@ -361,7 +370,7 @@ hmc_status hmc_apply_M(hmc_ctx* c, const double* phi, double ms, const void* in,
   HMC_TRY(check_vec(c, in, prec, "in"));
   HMC_TRY(check_vec(c, out, prec, "out"));
   HMC_TRY(check_mass(c, ms));
-  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  if (ranges_overlap(in, out, vec_bytes(c, prec))) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
   HMC_TRY(prepare_field(c, phi));
   if (prec == 64)
     return m_launch<double>(c, c->geo, c->delta * ms, (const double2*)in, nullptr, 0.0, (double2*)out);
@@ -374,7 +383,7 @@ hmc_status hmc_apply_Mdag(hmc_ctx* c, const double* phi, double ms, const void* 
   HMC_TRY(check_vec(c, in, prec, "in"));
   HMC_TRY(check_vec(c, out, prec, "out"));
   HMC_TRY(check_mass(c, ms));
-  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  if (ranges_overlap(in, out, vec_bytes(c, prec))) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
   HMC_TRY(prepare_field(c, phi));
   if (prec == 64) return mdag_launch<double>(c, c->geo, c->delta * ms, (const double2*)in, (double2*)out);
   return mdag_launch<float>(c, c->geo, (float)(c->delta * ms), (const float2*)in, (float2*)out);
@@ -388,7 +397,7 @@ hmc_status hmc_apply_MMdag(hmc_ctx* c, const double* phi, double ms, double sigm
   HMC_TRY(check_vec(c, out, prec, "out"));
   HMC_TRY(check_mass(c, ms));
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, HMC_ERR_INVALID, "sigma must be finite and >= 0");
-  if (in == out) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
+  if (ranges_overlap(in, out, vec_bytes(c, prec))) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
   HMC_TRY(prepare_field(c, phi));
   const size_t N = (size_t)c->geo.N;
   if (prec == 64) return apply_A64(c, ms, sigma, (const double2*)in, (double2*)out);
@@ -408,7 +417,7 @@ static hmc_status solve_checks(hmc_ctx* c, double ms, double sigma, const void* 
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, HMC_ERR_INVALID, "sigma must be finite and >= 0");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, HMC_ERR_INVALID, "tol must be positive");
   if (maxit < 1) return fail(c, HMC_ERR_INVALID, "maxit must be >= 1");
-  if (b == x) return fail(c, HMC_ERR_INVALID, "b and x must not overlap");
+  if (ranges_overlap(b, x, vec_bytes(c, prec))) return fail(c, HMC_ERR_INVALID, "b and x must not overlap");
   return HMC_OK;
 }
 

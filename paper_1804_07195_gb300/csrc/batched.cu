@@ -22,6 +22,7 @@
 
 #include "operator.cuh"
 #include "solvers.h"
+#include "validate.h"
 
 namespace hmc {
 
@@ -668,10 +669,8 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
   for (int s = 0; s < nsys; ++s) {
     const hmc_system& y = sys[s];
     const hmc_lattice& L = y.lat;
-    if (L.n < 1 || L.m < 1 || L.nt < 2 || !(L.beta > 0.0) || !std::isfinite(L.kappa))
-      return fail(c, HMC_ERR_INVALID, "bad lattice in batched system");
-    const long long N = 2LL * L.n * L.m * L.nt;
-    if (N >= (1LL << 30)) return fail(c, HMC_ERR_INVALID, "batched system too large");
+    if (bad_lattice(&L)) return fail(c, HMC_ERR_INVALID, "bad lattice in batched system");
+    const long long N = lattice_sites(&L);
     if (!y.phi || !y.b || !y.x || ((uintptr_t)y.b) % 16 || ((uintptr_t)y.x) % 16 || ((uintptr_t)y.phi) % 8)
       return fail(c, HMC_ERR_INVALID, "batched system has a NULL or misaligned pointer");
     if (!(y.sigma >= 0.0) || !(y.tol > 0.0) || y.maxit < 1 || !std::isfinite(y.ms))

@@ -228,6 +228,10 @@ inline int shape_grid(const hmc_ctx* c, int id, long long work) {
 // Instrumented launch: counts, and brackets with events when timing is on.
 void prof_begin(hmc_ctx* c, int id, cudaEvent_t* a);
 void prof_end(hmc_ctx* c, int id, cudaEvent_t a);
+// Forget the last n launches of kernel id (counters, algorithmic bytes and any
+// pending event pair): launches that found the solve finished and returned at
+// entry, so that the counters and timings cover only work that was done.
+void prof_discard_last(hmc_ctx* c, int id, long long n, double bytes_each);
 
 // `bytes`: algorithmic bytes of this launch; negative = the kernel's bytes per
 // site times the context's site count.

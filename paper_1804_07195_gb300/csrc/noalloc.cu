@@ -14,6 +14,7 @@
 
 #include "hmc.h"
 #include "operator.cuh"
+#include "validate.h"
 
 namespace hmc {
 namespace {
@@ -67,13 +68,15 @@ using namespace hmc;
 
 extern "C" hmc_status hmc_apply_MMdag_noalloc(const hmc_lattice* lat, const double* phi, double ms,
                                               double sigma, const void* in, void* out, void* cuda_stream) {
-  if (!lat || !phi || !in || !out) return HMC_ERR_INVALID;
-  if (lat->n < 1 || lat->m < 1 || lat->nt < 2 || !(lat->beta > 0.0) || !(lat->U > 0.0)) return HMC_ERR_INVALID;
-  if (((uintptr_t)phi) % 8 || ((uintptr_t)in) % 16 || ((uintptr_t)out) % 16 || in == out) return HMC_ERR_INVALID;
+  // every check runs before the first CUDA call: a rejected call touches no device
+  if (bad_lattice(lat)) return HMC_ERR_INVALID;  // the same checks as hmc_create
+  if (!phi || !in || !out) return HMC_ERR_INVALID;
+  const long long N = lattice_sites(lat);
+  if (((uintptr_t)phi) % 8 || ((uintptr_t)in) % 16 || ((uintptr_t)out) % 16) return HMC_ERR_INVALID;
+  if (ranges_overlap(in, out, (size_t)N * sizeof(double2))) return HMC_ERR_INVALID;
   if (!(sigma >= 0.0) || !std::isfinite(sigma) || !std::isfinite(ms)) return HMC_ERR_INVALID;
   const double delta = lat->beta / lat->nt;
   if (1.0 - delta * ms == 0.0) return HMC_ERR_INVALID;
-  const long long N = 2LL * lat->n * lat->m * lat->nt;
   if (N > (long long)HMC_NOALLOC_MAX_SITES) return HMC_ERR_NOMEM;  // beyond the static scratch
 
   int dev = 0;

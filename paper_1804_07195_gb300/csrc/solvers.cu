@@ -270,7 +270,9 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
       HMC_CUDA(c, cudaMemcpyAsync(c->loop_trips_host, c->loop_trips, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                   c->stream));
       HMC_CUDA(c, cudaStreamSynchronize(c->stream));
-      const double its = (double)c->loop_trips_host[0] * kChunk;
+      // the loop ran trips x kChunk iterations, of which sch->iter did work
+      // (the rest found the done flag set and returned at entry)
+      const double its = (double)sch->iter;
       for (int k = 0; k < nk; ++k) {
         c->prof.launches[kid[k]] += (long long)its;
         c->prof.bytes[kid[k]] += its * kbytes[k] * g.N;
@@ -312,8 +314,15 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
     HMC_CUDA(c, cudaStreamSynchronize(c->stream));
     if (sch->done != CG_RUNNING) break;
     if (launched > (long long)maxit + 2 * kChunk) break;  // cannot happen: the device stops at maxit
-    if (++checks >= 2 && per_check < 4) per_check *= 2;
+    // with per-launch timing on, check after every chunk so that few launches
+    // run past convergence
+    if (++checks >= 2 && per_check < 4 && !c->prof.timing) per_check *= 2;
   }
+  // Launches after convergence return at entry: drop them from the counters,
+  // the algorithmic bytes and the per-launch timings, so these cover exactly
+  // the sch->iter iterations that ran.
+  if (!persistent && !looped)
+    for (int k = 0; k < nk; ++k) prof_discard_last(c, kid[k], launched - (long long)sch->iter, kbytes[k] * g.N);
   st->iters += sch->iter;
   if (sizeof(R) == 8) st->applies64 += sch->iter; else st->applies32 += sch->iter;
   st->cg_done = sch->done;

@@ -149,6 +149,19 @@ def force_norm(g) -> float:
     return float(torch.linalg.vector_norm(g).item() / math.sqrt(g.numel()))
 
 
+def pair_forces(ctx, phi, rho, m0: float, m1: float, opts):
+    """The two forces Section 7.2 measures for the mass pair (m0, m1) of a
+    two-mass Hasenbusch action, as CUDA tensors: dS_1/dphi of the chi_1 term
+    (Eq. f_chi_i; its size enters Eq. small_force_eqn) and dS/dphi of the
+    Gaussian plus top term phi + chi_2 (Eq. large_force_eqn). The
+    pseudofermions come from the heat-bath vectors rho at the field phi."""
+    from . import _abi
+    chis, _ = ctx.make_chi(phi, [m0, m1], rho, opts=opts)
+    F1, _ = ctx.force(phi, [m0, m1], chis, term=1, flags=_abi.HMC_FERMION, opts=opts)
+    F2, _ = ctx.force(phi, [m0, m1], chis, term=2, flags=_abi.HMC_FERMION | _abi.HMC_GAUSSIAN, opts=opts)
+    return F1, F2
+
+
 def measure_and_tune(ctx, phi, rho, solve_masses: Sequence[float] = (0.05, 0.1, 0.2, 0.4, 0.8, 1.5, 3.0),
                      pairs: Sequence[Tuple[float, float]] = SECTION_7_2_MASS_PAIRS, tol: float = 1e-10,
                      repeats: int = 2) -> TuneResult:
@@ -175,9 +188,7 @@ def measure_and_tune(ctx, phi, rho, solve_masses: Sequence[float] = (0.05, 0.1, 
     t0, lmax, lmin = fit_solver_time(solve_masses, times)
     small_mu0, small_mu1, small_F, top_ms, top_F = [], [], [], [], []
     for (m0, m1) in pairs:
-        chis, _ = ctx.make_chi(phi, [m0, m1], rho, opts=opts)
-        F1, _ = ctx.force(phi, [m0, m1], chis, term=1, flags=_abi.HMC_FERMION, opts=opts)
-        F2, _ = ctx.force(phi, [m0, m1], chis, term=2, flags=_abi.HMC_FERMION | _abi.HMC_GAUSSIAN, opts=opts)
+        F1, F2 = pair_forces(ctx, phi, rho, m0, m1, opts)
         small_mu0.append(m0)
         small_mu1.append(m1)
         small_F.append(force_norm(F1))

@@ -67,6 +67,8 @@ def test_product_never_imports_the_oracle():
 @pytest.mark.parametrize("params", [
     (4096, 4096, 32, 1.0, 2.0, 4.0),          # exactly 2^30 sites: above the index range
     (1 << 20, 1 << 20, 1 << 20, 1.0, 2.0, 4.0),  # n*m*nt overflows 32 bits
+    (5, (1 << 30) + 1, 1 << 30, 1.0, 2.0, 4.0),  # 2*n*m*nt overflows signed 64 bits
+    ((1 << 31) - 1, (1 << 31) - 1, (1 << 31) - 1, 1.0, 2.0, 4.0),  # every factor at the int limit
     (3, 3, 8, float("nan"), 2.0, 4.0),
     (3, 3, 8, 1.0, float("inf"), 4.0),
     (3, 3, 8, 1.0, 2.0, 0.0),
@@ -106,3 +108,44 @@ def test_every_status_has_its_own_message(lib):
     assert all(m and m != b"unknown status" for m in msgs) and len(set(msgs)) == len(codes)
     assert L.hmc_status_string(-99) == b"unknown status"
     assert L.hmc_last_error(None) == b""
+
+
+# 16-byte aligned stand-ins for device pointers: every lattice below is rejected
+# before the first CUDA call, so none of them is ever dereferenced
+FAKE_PHI, FAKE_IN, FAKE_OUT = 0x10000, 0x20000000, 0x40000000
+
+
+@pytest.mark.parametrize("params", [
+    (5, (1 << 30) + 1, 1 << 30, 1.0, 2.0, 4.0),
+    (4096, 4096, 32, 1.0, 2.0, 4.0),
+    (3, 3, 8, float("nan"), 2.0, 4.0),
+    (3, 3, 8, 1.0, 2.0, float("inf")),
+    (3, 3, 8, 1.0, 0.0, 4.0),
+    (0, 3, 8, 1.0, 2.0, 4.0),
+])
+def test_noalloc_rejects_what_create_rejects(lib, params):
+    """The allocation-free entry point validates its lattice with the same
+    checks as hmc_create (overflow-safe sizes, finite couplings), before any
+    CUDA call."""
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    lat = _abi.hmc_lattice(*params)
+    h = ctypes.c_void_p()
+    assert L.hmc_create(ctypes.byref(h), ctypes.byref(lat), None) == _abi.HMC_ERR_INVALID
+    st = L.hmc_apply_MMdag_noalloc(ctypes.byref(lat), ctypes.c_void_p(FAKE_PHI), 0.0, 0.0,
+                                   ctypes.c_void_p(FAKE_IN), ctypes.c_void_p(FAKE_OUT), None)
+    assert st == _abi.HMC_ERR_INVALID
+
+
+@pytest.mark.parametrize("shift_bytes", [0, 16, 16 * 8])
+def test_noalloc_rejects_overlapping_vectors(lib, shift_bytes):
+    """in and out that share any byte (not only identical pointers) are rejected."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("CPU-only check with stand-in pointers")
+    from paper_1804_07195_gb300 import _abi
+    L = _abi.load()
+    lat = _abi.hmc_lattice(3, 3, 8, 1.0, 2.0, 4.0)
+    st = L.hmc_apply_MMdag_noalloc(ctypes.byref(lat), ctypes.c_void_p(FAKE_PHI), 0.0, 0.0,
+                                   ctypes.c_void_p(FAKE_IN), ctypes.c_void_p(FAKE_IN + shift_bytes), None)
+    assert st == _abi.HMC_ERR_INVALID

@@ -74,7 +74,7 @@ def test_batch_of_48_lattices(mixed):
         for ms, b in zip(w.masses, w.rho):
             inst.append((w, ms, 0.0, b))
     xs, infos = run_batch(inst, mixed)
-    # check a spread of systems against the oracle operator, all via the report
-    assert all(i["true_rel_res"] <= 1e-10 for i in infos)
-    pick = list(range(0, len(inst), 11))
-    check([inst[k] for k in pick], [xs[k] for k in pick], [infos[k] for k in pick], 1e-10)
+    # every one of the 144 systems: its true residual evaluated with the
+    # oracle's operator on its own lattice, and the library's report of it
+    assert len(inst) == 144
+    check(inst, xs, infos, 1e-10)

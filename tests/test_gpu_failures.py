@@ -77,6 +77,33 @@ def test_invalid_arguments():
             ctx.apply_M(phi, 0.0, b[:-1])  # wrong length is caught in the binding
 
 
+def test_partially_overlapping_vectors_are_rejected():
+    """in/out (and b/x) ranges that share some entries, not only identical
+    pointers, are rejected with HMC_ERR_INVALID before any launch; disjoint
+    parts of one buffer are accepted."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.small(3, 3, 4, seed=3)
+    N = w.lat.nsites
+    with ctx_for(w.lat) as ctx:
+        phi = dev(w.phi)
+        for dt in (torch.complex128, torch.complex64):
+            buf = torch.zeros(2 * N, dtype=dt, device="cuda")
+            buf[:N] = dev(w.b).to(dt)
+            for shift in (1, N // 2, N - 1):
+                for fn in (ctx.apply_M, ctx.apply_Mdag, ctx.apply_MMdag):
+                    with pytest.raises(hmc.HMCError) as e:
+                        fn(phi, 0.0, buf[:N], out=buf[shift:shift + N])
+                    assert e.value.status == -1
+            ctx.apply_MMdag(phi, 0.0, buf[:N], out=buf[N:])  # disjoint: fine
+        buf = torch.zeros(2 * N, dtype=torch.complex128, device="cuda")
+        buf[:N] = dev(w.b)
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_cg(phi, 0.0, buf[:N], x=buf[3:3 + N])
+        assert e.value.status == -1
+        torch.cuda.synchronize()
+
+
 def test_bad_batched_descriptor():
     need_gpu()
     import paper_1804_07195_gb300 as hmc

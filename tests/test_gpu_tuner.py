@@ -32,6 +32,38 @@ def test_tuner_end_to_end():
     assert res.N[0] == res.N[1] >= 1
 
 
+@pytest.mark.parametrize("pair", [(0.1, 0.3), (0.2, 1.5)])
+def test_tuner_forces_match_the_oracle(pair):
+    """The force vectors behind the tuner's F_chi1 and F_top (tuner.pair_forces,
+    the function measure_and_tune calls) at 12x12, nt=32 against the oracle:
+    pseudofermions from oracle.action.make_chi, then oracle.action.term_grad of
+    the chi_1 term and of the top term plus the Gaussian gradient, all with
+    sparse-LU solves; element by element within 1e-7 of the largest entry
+    (library solves at 1e-12, FP64-outer mixed FGMRES as in the tuner)."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    from paper_1804_07195_gb300 import tuner
+    from oracle import action as oa
+    from oracle.lattice import Lattice as OLat
+    from gpu_util import host, rel_max
+    w = W.workload("L12x12x32")
+    ol = OLat.from_params(w.lat)
+    m0, m1 = pair
+    solve = oa.SolveA(ol, "splu")
+    chis = oa.make_chi(ol, w.phi, [m0, m1], w.rho, solve)
+    F1_ref = oa.term_grad(ol, w.phi, [m0, m1], chis, 1, solve)
+    F2_ref = oa.term_grad(ol, w.phi, [m0, m1], chis, 2, solve) + oa.grad_gaussian(ol, w.phi)
+    opts = hmc.SolverOpts(method=hmc._abi.HMC_SOLVER_FGMRES_MIXED, tol=1e-12)
+    with ctx_for(w.lat) as ctx:
+        F1, F2 = tuner.pair_forces(ctx, dev(w.phi), [dev(r) for r in w.rho], m0, m1, opts)
+        F1, F2 = host(F1), host(F2)
+    assert rel_max(F1, F1_ref) <= 1e-7
+    assert rel_max(F2, F2_ref) <= 1e-7
+    # and the sizes the tuner fits (root mean square over sites)
+    for got, ref in ((F1, F1_ref), (F2, F2_ref)):
+        assert abs(np.sqrt(np.mean(got ** 2)) - np.sqrt(np.mean(ref ** 2))) <= 1e-7 * np.sqrt(np.mean(ref ** 2))
+
+
 def test_nmd_tuner_on_the_four_site_model(paper):
     """Algorithm B.1 driving real trajectories (4-site model, nt = 64, where
     the Omelyan integrator is unstable at N_MD = 8 and stable at 16): the tuned

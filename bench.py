@@ -205,7 +205,8 @@ def main():
                     help="2 = each CG solve one graph launch with a device-side loop (default); 1 = graph "
                          "chunks with host checks, the mode kernel profilers can see into")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream",
+                             "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -475,17 +476,18 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
     """Operator applications alone: M, M^dagger and M M^dagger in FP32 and FP64
     on the 102x102x64 lattice (its vectors stay in the 135 MB L2 between
     applications) and on a 306x306x64 lattice (12M sites, L2 flushed before
-    every application, so each one streams from HBM). Kernel time comes from
-    the library's CUDA events around each launch (no host call overhead).
-    Algorithmic bytes per site of one M or M^dagger: FP32 reads the vector
-    (8 B) and phi as float (4 B) and writes 8 B; FP64 reads the vector (16 B)
-    and the phase table e^{i phi} (16 B) and writes 16 B; M M^dagger is the
-    two in sequence."""
+    every application, so each one streams from HBM). M M^dagger runs in both
+    designs: two passes (u = M^dagger x written to memory and read back) and
+    the fused kernel (u kept on chip). Kernel time comes from the library's
+    CUDA events around each launch (no host call overhead). frac_hbm counts
+    the algorithmic bytes per site of the operation -- what it must move: the
+    vector in and out and phi (FP32: 8 + 8 + 4 = 20 B; FP64: 16 + 16 + 8 =
+    40 B), the same for M, M^dagger and M M^dagger -- against the measured
+    copy peak."""
     out = {}
-    per_site = {32: 20.0, 64: 48.0}
-    kernels = {("M", 32): ["apply_M_f32"], ("Mdag", 32): ["apply_Mdag_f32"],
-               ("MMdag", 32): ["apply_Mdag_f32", "apply_M_f32"], ("M", 64): ["apply_M_f64"],
-               ("Mdag", 64): ["apply_Mdag_f64"], ("MMdag", 64): ["apply_Mdag_f64", "apply_M_f64"]}
+    per_site = {32: 20.0, 64: 40.0}
+    kernels = {"M": ["apply_M_f{p}"], "Mdag": ["apply_Mdag_f{p}"],
+               "MMdag_two_pass": ["apply_Mdag_f{p}", "apply_M_f{p}"], "MMdag_fused": ["mmdag_fused_f{p}"]}
     for name, (n, m, nt) in (("l2_resident_102x102x64", (102, 102, 64)), ("streaming_306x306x64", (306, 306, 64))):
         lat = hmc.Lattice(n, m, nt, 1.0, 3.8, 12.0)
         N = lat.nsites
@@ -497,9 +499,13 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
             for prec in (32, 64):
                 ct = torch.complex64 if prec == 32 else torch.complex128
                 x = torch.randn(N, dtype=ct, device="cuda")
-                for op in ("M", "Mdag", "MMdag"):
-                    fn = {"M": lambda: ctx.apply_M(None, 0.1, x), "Mdag": lambda: ctx.apply_Mdag(None, 0.1, x),
-                          "MMdag": lambda: ctx.apply_MMdag(None, 0.1, x)}[op]
+                for op in ("M", "Mdag", "MMdag_two_pass", "MMdag_fused"):
+                    if op == "MMdag_two_pass":
+                        ctx.set_apply_variant(1)
+                    elif op == "MMdag_fused":
+                        ctx.set_apply_variant(2)
+                    fn = {"M": lambda: ctx.apply_M(None, 0.1, x), "Mdag": lambda: ctx.apply_Mdag(None, 0.1, x)}.get(
+                        op, lambda: ctx.apply_MMdag(None, 0.1, x))
                     for _ in range(3):
                         fn()
                     torch.cuda.synchronize()
@@ -512,15 +518,20 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                     torch.cuda.synchronize()
                     prof = ctx.profile_read()
                     ctx.profile(False, reset=True)
-                    t = sum(prof[k]["ms"] for k in kernels[(op, prec)]) * 1e-3 / reps
-                    nbytes = per_site[prec] * N * (2 if op == "MMdag" else 1)
-                    rows[f"{op}_f{prec}"] = {"us": t * 1e6, "gsite_s": N / t / 1e9, "gb_s": nbytes / t / 1e9,
-                                            "frac_hbm": nbytes / t / 1e9 / hbm}
+                    t = sum(prof[k.format(p=prec)]["ms"] for k in kernels[op]) * 1e-3 / reps
+                    nbytes = per_site[prec] * N
+                    row = {"us": t * 1e6, "gsite_s": N / t / 1e9, "gb_s": nbytes / t / 1e9,
+                           "frac_hbm": nbytes / t / 1e9 / hbm}
+                    if op == "MMdag_fused":
+                        row["tile"] = dict(zip(("Ti", "Tj", "Tt", "depth", "pairs"), ctx.fused_tile(prec)))
+                    rows[f"{op}_f{prec}"] = row
+                ctx.set_apply_variant(0)
                 del x
         out[name] = {"sites": N, **rows}
     out["note"] = ("mean kernel time of 20 applications (CUDA events around each launch inside the library); "
                    "the streaming lattice flushes L2 before every application; frac_hbm = algorithmic bytes "
-                   "/ time / measured copy peak")
+                   "(20 B/site FP32, 40 B/site FP64, also for M M^dagger) / time / measured copy peak; the "
+                   "fused tile is the one the library's tuner chose for this lattice")
     return out
 
 
@@ -606,8 +617,9 @@ def kernel_case(case, graph_mode=2):
     from paper_1804_07195_gb300 import build
     import workloads as W
     build.build()
-    if case == "mmdag32_stream":
-        # 306x306x64 (12M sites): vectors far larger than L2, L2 flushed before each application
+    if case in ("mmdag32_stream", "mmdag32_stream_fused"):
+        # 306x306x64 (12M sites): vectors far larger than L2, L2 flushed before each
+        # application; two passes, or the fused kernel on a pinned tile (no tuning launches)
         lat = hmc.Lattice(306, 306, 64, 1.0, 3.8, 12.0)
         g = W.rng(9306)
         phi = torch.tensor(g.normal(0.0, math.sqrt(lat.delta * 3.8), lat.nsites), device="cuda")
@@ -615,6 +627,11 @@ def kernel_case(case, graph_mode=2):
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         with hmc.Context(lat) as ctx:
             ctx.load_field(phi)
+            if case == "mmdag32_stream_fused":
+                ctx.set_apply_variant(2)
+                ctx.set_fused_tile(32, *FUSED_STREAM_TILE)
+            else:
+                ctx.set_apply_variant(1)
             for _ in range(8):
                 flush.zero_()
                 ctx.apply_MMdag(None, 0.1, x)
@@ -659,6 +676,9 @@ def kernel_case(case, graph_mode=2):
         torch.cuda.synchronize()
     print(json.dumps({"case": case, **{k: v for k, v in info.items()}}))
 
+
+# fused M M^dagger tile of the streaming kernel profile: Ti, Tj, Tt, depth, pairs
+FUSED_STREAM_TILE = (28, 6, 64, 2, 1)
 
 # the translation unit of the FP32 CG pair (the kernels whose DRAM traffic
 # profiles/traffic.json records): kernels.cu and everything it includes

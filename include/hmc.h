@@ -292,6 +292,31 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
  * Setting it re-runs the tuner at the next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
+/* M M^dagger applications (hmc_apply_MMdag) run in one of two designs:
+ * 1 = two passes, u = M^dagger in written to and read back from memory, then
+ * M u + sigma in; 2 = one fused kernel: each block stages the time slices of a
+ * tile of cells plus a one-cell ring in shared memory (cp.async, two slices
+ * ahead), forms u there and applies M to it, so u never reaches memory
+ * (20 bytes per site in FP32, 48 in FP64, against 40 and 96 for two passes).
+ * variant 0 (default) times both on the first application in each precision
+ * and keeps the faster; 1 or 2 pins one. Results agree to rounding order. */
+hmc_status hmc_set_apply_variant(hmc_ctx* ctx, int variant);
+/* The variant used for precision prec (0 = not chosen yet). */
+hmc_status hmc_apply_variant(hmc_ctx* ctx, int prec, int* variant);
+/* Pin the fused kernel's tile for precision prec: Ti x Tj cells per block
+ * (clamped to the lattice), Tt time slices per block, `depth` time slices
+ * staged ahead of the one in use (2 or 6), and pairs = 1 for the FP32 kernel
+ * whose threads own two neighbouring cells as one 16-byte complex64 pair
+ * (n and Ti even; (Ti/2+2)(Tj+2) <= 256 threads) or 0 for one cell per thread
+ * ((Ti+2)(Tj+2) <= 1024 threads in FP32, 512 in FP64). Without it the tile
+ * is chosen by timing candidates on the first fused application. A call whose
+ * vectors are not 16-byte aligned runs the one-cell kernel. HMC_ERR_INVALID
+ * when the tile does not fit (threads, shared memory, parity). */
+hmc_status hmc_set_fused_tile(hmc_ctx* ctx, int prec, int Ti, int Tj, int Tt, int depth, int pairs);
+/* The fused kernel's tile in use for precision prec (zeros before the first
+ * fused application). */
+hmc_status hmc_fused_tile(hmc_ctx* ctx, int prec, int* Ti, int* Tj, int* Tt, int* depth, int* pairs);
+
 /* Test hook for the bounded waits of the persistent FP32 CG kernel (variant 4
  * above): from the next persistent solve on, every grid barrier waits for
  * `extra` more arrivals than the launch has blocks (with extra > 0 no barrier

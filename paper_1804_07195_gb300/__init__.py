@@ -296,6 +296,28 @@ class Context:
         3: marching; 4: persistent (one cooperative launch per solve)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
+    def set_apply_variant(self, variant: int):
+        """M M^dagger applications: 0 = choose by timing (default), 1 = two
+        passes through memory, 2 = the fused kernel (u kept on chip)."""
+        self._check(self.lib.hmc_set_apply_variant(self.h, variant))
+
+    def apply_variant(self, prec: int) -> int:
+        v = C.c_int()
+        self._check(self.lib.hmc_apply_variant(self.h, prec, C.byref(v)))
+        return v.value
+
+    def set_fused_tile(self, prec: int, Ti: int, Tj: int, Tt: int, depth: int = 2, pairs: int = 0):
+        """Pin the fused kernel's tile: Ti x Tj cells and Tt time slices per
+        block, `depth` slices staged ahead (2 or 6), pairs = 1 for the FP32
+        kernel with two cells per thread (n and Ti even)."""
+        self._check(self.lib.hmc_set_fused_tile(self.h, prec, Ti, Tj, Tt, depth, pairs))
+
+    def fused_tile(self, prec: int):
+        """(Ti, Tj, Tt, depth, pairs) of the fused kernel in use for precision prec."""
+        v = [C.c_int() for _ in range(5)]
+        self._check(self.lib.hmc_fused_tile(self.h, prec, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def graph_mode(self) -> int:
         """2: one graph launch per CG solve (device-side loop); 1: captured
         chunks with host checks; 0: kernels launched one by one."""

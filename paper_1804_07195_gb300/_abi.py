@@ -103,6 +103,10 @@ PROTOTYPES = {
                               C.POINTER(hmc_solver_opts), C.POINTER(hmc_solver_opts),
                               C.POINTER(D), C.POINTER(D), C.POINTER(hmc_solve_info)]),
     "hmc_set_cg_variant": (S, [P, I]),
+    "hmc_set_apply_variant": (S, [P, I]),
+    "hmc_apply_variant": (S, [P, I, C.POINTER(I)]),
+    "hmc_set_fused_tile": (S, [P, I, I, I, I, I, I]),
+    "hmc_fused_tile": (S, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
     "hmc_set_wait_test": (S, [P, I, C.c_longlong]),
     "hmc_graph_mode": (S, [P, C.POINTER(I)]),
     "hmc_set_graph_mode": (S, [P, I]),

@@ -251,6 +251,57 @@ static hmc_status check_prec(hmc_ctx* c, int prec) {
   return HMC_OK;
 }
 
+// (M M^dagger + sigma) in, in two passes (u = M^dagger in through memory) or
+// with the fused kernel (u on chip).
+template <typename R>
+static hmc_status apply_A_variant(hmc_ctx* c, int variant, double ms, double sigma, const V2<R>* in,
+                                  V2<R>* out) {
+  const R dm = (R)(c->delta * ms);
+  if (variant == 2) return mmdag_fused_launch<R>(c, c->geo, dm, (R)sigma, in, out);
+  if constexpr (sizeof(R) == 8) {
+    return apply_A64(c, ms, sigma, in, out);
+  } else {
+    float2* u;
+    HMC_TRY(ws_get(c, WS_U32, sizeof(float2) * (size_t)c->geo.N, (void**)&u));
+    HMC_TRY(mdag_launch<float>(c, c->geo, dm, in, u));
+    return m_launch<float>(c, c->geo, dm, u, sigma != 0.0 ? in : nullptr, (float)sigma, out);
+  }
+}
+
+// The variant in use: pinned by hmc_set_apply_variant, else chosen on the
+// first application in each precision by timing both (after tuning the fused
+// kernel's tile on the same operands).
+template <typename R>
+static hmc_status apply_A(hmc_ctx* c, double ms, double sigma, const V2<R>* in, V2<R>* out) {
+  const int pi = sizeof(R) == 4 ? 0 : 1;
+  int v = c->apply_variant;
+  if (v == 0) {
+    if (c->apply_choice[pi] == 0) {
+      float best = 1e30f;
+      cudaEvent_t e0, e1;
+      HMC_CUDA(c, cudaEventCreate(&e0));
+      HMC_CUDA(c, cudaEventCreate(&e1));
+      for (int cand = 1; cand <= 2; ++cand) {
+        HMC_TRY(apply_A_variant<R>(c, cand, ms, sigma, in, out));  // warm (and tune)
+        HMC_CUDA(c, cudaEventRecord(e0, c->stream));
+        for (int rep = 0; rep < 3; ++rep) HMC_TRY(apply_A_variant<R>(c, cand, ms, sigma, in, out));
+        HMC_CUDA(c, cudaEventRecord(e1, c->stream));
+        HMC_CUDA(c, cudaEventSynchronize(e1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) {
+          best = t;
+          c->apply_choice[pi] = cand;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    v = c->apply_choice[pi];
+  }
+  return apply_A_variant<R>(c, v, ms, sigma, in, out);
+}
+
 extern "C" {
 
 int hmc_abi_version(void) { return HMC_ABI_VERSION; }
@@ -399,14 +450,8 @@ hmc_status hmc_apply_MMdag(hmc_ctx* c, const double* phi, double ms, double sigm
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, HMC_ERR_INVALID, "sigma must be finite and >= 0");
   if (ranges_overlap(in, out, vec_bytes(c, prec))) return fail(c, HMC_ERR_INVALID, "in and out must not overlap");
   HMC_TRY(prepare_field(c, phi));
-  const size_t N = (size_t)c->geo.N;
-  if (prec == 64) return apply_A64(c, ms, sigma, (const double2*)in, (double2*)out);
-  float2* u;
-  HMC_TRY(ws_get(c, WS_U32, sizeof(float2) * N, (void**)&u));
-  const float dm = (float)(c->delta * ms);
-  HMC_TRY(mdag_launch<float>(c, c->geo, dm, (const float2*)in, u));
-  return m_launch<float>(c, c->geo, dm, u, sigma != 0.0 ? (const float2*)in : nullptr, (float)sigma,
-                         (float2*)out);
+  if (prec == 64) return apply_A<double>(c, ms, sigma, (const double2*)in, (double2*)out);
+  return apply_A<float>(c, ms, sigma, (const float2*)in, (float2*)out);
 }
 
 static hmc_status solve_checks(hmc_ctx* c, double ms, double sigma, const void* b, void* x, int prec,
@@ -503,6 +548,41 @@ hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   c->tuned32 = false;
   c->persist32 = false;
   destroy_graphs(c);
+  return HMC_OK;
+}
+
+hmc_status hmc_set_apply_variant(hmc_ctx* c, int variant) {
+  if (!c) return HMC_ERR_INVALID;
+  if (variant < 0 || variant > 2) return fail(c, HMC_ERR_INVALID, "variant must be 0, 1 or 2");
+  c->apply_variant = variant;
+  c->apply_choice[0] = c->apply_choice[1] = 0;
+  return HMC_OK;
+}
+
+hmc_status hmc_apply_variant(hmc_ctx* c, int prec, int* variant) {
+  if (!c || !variant) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  *variant = c->apply_variant ? c->apply_variant : c->apply_choice[prec == 32 ? 0 : 1];
+  return HMC_OK;
+}
+
+hmc_status hmc_set_fused_tile(hmc_ctx* c, int prec, int Ti, int Tj, int Tt, int depth, int pairs) {
+  if (!c) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  if (Ti < 1 || Tj < 1 || Tt < 1) return fail(c, HMC_ERR_INVALID, "tile sizes must be >= 1");
+  if (pairs != 0 && pairs != 1) return fail(c, HMC_ERR_INVALID, "pairs must be 0 or 1");
+  return set_fused_shape(c, prec, Ti, Tj, Tt, depth, pairs);
+}
+
+hmc_status hmc_fused_tile(hmc_ctx* c, int prec, int* Ti, int* Tj, int* Tt, int* depth, int* pairs) {
+  if (!c || !Ti || !Tj || !Tt || !depth || !pairs) return HMC_ERR_INVALID;
+  HMC_TRY(check_prec(c, prec));
+  const FusedShape& fs = c->fshape[prec == 32 ? 0 : 1];
+  *Ti = fs.Ti;
+  *Tj = fs.Tj;
+  *Tt = fs.Tt;
+  *depth = fs.D;
+  *pairs = fs.pairs;
   return HMC_OK;
 }
 

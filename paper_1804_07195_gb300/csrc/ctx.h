@@ -44,6 +44,8 @@ enum KernelId {
   K_BATCH_RESID,
   K_BATCH_MISC,
   K_CG_PERSIST32,
+  K_MMDAG_FUSED32,
+  K_MMDAG_FUSED64,
   K_COUNT
 };
 
@@ -88,6 +90,15 @@ struct Shape {
   int tiled = 0;   // FP32 CG pair: 1 = shared-memory tiled kernels, 2 = marching kernels
                    // (threads = cells per block)
   int tt = 1;      // tiled or marching: time slices per block
+};
+
+// Tile of the fused M M^dagger kernel (fused.cu): Ti x Tj cells per block
+// (plus a one-cell ring), Tt time slices per block.
+struct FusedShape {
+  int Ti = 0, Tj = 0, Tt = 0;
+  int tiles_i = 0, tiles_j = 0, tiles_t = 0;
+  int D = 2;  // time slices staged ahead of the one in use
+  int pairs = 0;  // FP32: two cells per thread (n and Ti even; 16-byte aligned vectors)
 };
 
 struct ProfileState {
@@ -136,6 +147,12 @@ struct hmc_ctx {
   int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching,
                          // 4 persistent
   bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
+  // M M^dagger applications: 0 = choose per precision by timing on first use,
+  // 1 = two passes (M^dagger to memory, then M), 2 = the fused kernel
+  int apply_variant = 0;
+  int apply_choice[2] = {0, 0};     // FP32, FP64: the variant in use (0 = not chosen yet)
+  hmc::FusedShape fshape[2];        // FP32, FP64 tiles of the fused kernel
+  bool fused_tuned[2] = {false, false};
   // device and pinned host buffers of the batched solver, kept across calls
   // (slot i holds the i-th buffer a call asks for; grown when too small)
   static constexpr int kBatchSlots = 40;

@@ -18,7 +18,8 @@ const char* const kKernelNames[K_COUNT] = {
     "cg_p_f32",       "residual_f64",   "residual_f32",  "cg_init0",       "convert",
     "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
     "force",          "axpy",           "md_update",     "batch_cg_graph_f64", "batch_cg_graph_f32",
-    "batch_init",     "batch_residual", "batch_misc",   "cg_persist_f32"};
+    "batch_init",     "batch_residual", "batch_misc",   "cg_persist_f32", "mmdag_fused_f32",
+    "mmdag_fused_f64"};
 
 const double kKernelBytesPerSite[K_COUNT] = {
     8 + 16 + 4,          // phase: phi in, E and phi32 out
@@ -45,7 +46,9 @@ const double kKernelBytesPerSite[K_COUNT] = {
     24,                  // axpy
     24,                  // md update
     192, 96, 16 * 4, 16 * 5, 0,
-    0};  // persistent CG: 56 B per site and iteration, counted after the solve
+    0,                   // persistent CG: 56 B per site and iteration, counted after the solve
+    8 + 4 + 8,           // fused M M^dagger f32: p, phi32, out (u stays on chip)
+    16 + 16 + 16};       // fused M M^dagger f64: p, E, out
 
 // ---------------------------------------------------------------------------
 // e^{i phi} for the FP64 stencils of Eq. ferm_op, and phi rounded to float.

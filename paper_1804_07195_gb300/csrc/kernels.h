@@ -19,6 +19,18 @@ template <typename R>
 hmc_status m_launch(hmc_ctx* c, const Geo& g, R dm, const V2<R>* u, const V2<R>* y, R sigma,
                     V2<R>* out);
 
+// out = (M M^dagger + sigma) in in one pass, u = M^dagger in kept on chip
+// (fused.cu); the tile shape is tuned on the first call per precision.
+template <typename R>
+hmc_status mmdag_fused_launch(hmc_ctx* c, const Geo& g, R dm, R sigma, const V2<R>* in, V2<R>* out);
+FusedShape make_fused_shape(const Geo& g, int Ti, int Tj, int Tt, int D, int pairs);
+template <typename R>
+bool fused_ok(const Geo& g, const FusedShape& fs);
+// Pin the fused kernel's tile, prefetch depth D (2 or 6) and, for FP32, the
+// two-cells-per-thread kernel (pairs) for prec 32 or 64; HMC_ERR_INVALID if
+// it does not fit.
+hmc_status set_fused_shape(hmc_ctx* c, int prec, int Ti, int Tj, int Tt, int D, int pairs);
+
 // CG building blocks on the state sc (see common.cuh).
 template <typename R>
 hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,

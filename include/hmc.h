@@ -286,10 +286,14 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
  * persistent kernel that runs the whole solve in one cooperative launch with
  * grid barriers (bounded waits; a wait that gives up returns
  * HMC_ERR_TIMEOUT) and keeps x and its own entries of r and p in shared
- * memory. variant: 0 = let the autotuner choose among all four (default),
- * 1 = grid-stride only, 2 = tiled only, 3 = marching only, 4 = persistent
- * (2 to 4 fall back to grid-stride where they do not fit the lattice).
- * Setting it re-runs the tuner at the next FP32 solve. */
+ * memory. The grid-stride pair also comes with two cells per thread: the
+ * neighbouring cells (i, i+1), i even, of a row, whose complex64 values are one
+ * 16-byte access in every vector (n even only). variant: 0 = let the
+ * autotuner choose among all of them (default), 1 = grid-stride with one
+ * cell per thread, 2 = tiled only, 3 = marching only, 4 = persistent,
+ * 5 = grid-stride with two cells per thread (2 to 5 fall back to variant 1
+ * where they do not fit the lattice). Setting it re-runs the tuner at the
+ * next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
 /* M M^dagger applications (hmc_apply_MMdag) run in one of two designs:
@@ -352,6 +356,9 @@ typedef struct {
                            -tt: the tiled FP32 CG kernels with tt time slices
                            per tile of `threads` cells; -(1000 + tt): the
                            marching kernels, tt slices per block */
+  int design;           /* FP32 CG kernels: 0 grid-stride (one cell per thread),
+                           1 tiled, 2 marching, 4 grid-stride with two cells
+                           per thread */
 } hmc_kernel_stat;
 
 /* Per-kernel launch counters are always kept. With timing on, every launch of

@@ -346,7 +346,8 @@ class Context:
         self._check(self.lib.hmc_profile_read(self.h, arr, _abi.HMC_NKERNELS, C.byref(cnt)))
         return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms_total,
                                        "bytes": arr[i].bytes_total,
-                                       "threads": arr[i].threads, "waves": arr[i].waves}
+                                       "threads": arr[i].threads, "waves": arr[i].waves,
+                                       "design": arr[i].design}
                 for i in range(cnt.value)}
 
 

@@ -65,7 +65,7 @@ class hmc_system(C.Structure):
 
 class hmc_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("ms_total", C.c_double),
-                ("bytes_total", C.c_double), ("threads", C.c_int), ("waves", C.c_int)]
+                ("bytes_total", C.c_double), ("threads", C.c_int), ("waves", C.c_int), ("design", C.c_int)]
 
 
 HMC_NKERNELS = 32

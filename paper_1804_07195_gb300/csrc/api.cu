@@ -506,7 +506,13 @@ hmc_status hmc_solve_spcg(hmc_ctx* c, const double* phi, double ms, double sigma
   HMC_TRY(solve_checks(c, ms, sigma, b, x, 32, tol, maxit));
   HMC_TRY(prepare_field(c, phi));
   SolveStats s;
-  hmc_status st = cg_core<float>(c, ms, sigma, (const float2*)b, (float2*)x, true, tol, maxit, 1, true, &s);
+  // the kernels with two cells per thread access x in 16-byte units: an x
+  // that is only 8-byte aligned is solved in a workspace vector and copied
+  float2* xs = (float2*)x;
+  if ((uintptr_t)x % 16) HMC_TRY(ws_get(c, WS_CG_X32, sizeof(float2) * (size_t)c->geo.N, (void**)&xs));
+  hmc_status st = cg_core<float>(c, ms, sigma, (const float2*)b, xs, true, tol, maxit, 1, true, &s);
+  if (xs != (float2*)x)
+    HMC_CUDA(c, cudaMemcpyAsync(x, xs, sizeof(float2) * (size_t)c->geo.N, cudaMemcpyDeviceToDevice, c->stream));
   fill_info(info, s, st, t0, 0, c->geo.N);
   return st;
 }
@@ -543,7 +549,7 @@ hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma,
 
 hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   if (!c) return HMC_ERR_INVALID;
-  if (variant < 0 || variant > 4) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 4");
+  if (variant < 0 || variant > 5) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 5");
   c->cg32_variant = variant;
   c->tuned32 = false;
   c->persist32 = false;
@@ -632,7 +638,9 @@ hmc_status hmc_profile_read(hmc_ctx* c, hmc_kernel_stat* out, int max, int* coun
     out[n].ms_total = c->prof.ms[i];
     out[n].bytes_total = c->prof.bytes[i];
     out[n].threads = c->shape[i].threads;
-    out[n].waves = c->shape[i].tiled ? -(c->shape[i].tt + (c->shape[i].tiled == 2 ? 1000 : 0)) : c->shape[i].waves;
+    const Shape& sh = c->shape[i];
+    out[n].waves = (sh.tiled == 1 || sh.tiled == 2) ? -(sh.tt + (sh.tiled == 2 ? 1000 : 0)) : sh.waves;
+    out[n].design = sh.tiled;
     ++n;
   }
   *count = n;

@@ -88,7 +88,8 @@ struct Shape {
   int waves = 1;
   int occ = 8;     // resident blocks per SM at this block size
   int tiled = 0;   // FP32 CG pair: 1 = shared-memory tiled kernels, 2 = marching kernels
-                   // (threads = cells per block)
+                   // (threads = cells per block), 4 = grid-stride kernels with two cells
+                   // per thread (16-byte accesses; n even)
   int tt = 1;      // tiled or marching: time slices per block
 };
 
@@ -227,7 +228,8 @@ inline long long cg32_part_capacity(const hmc_ctx* c) { return (long long)c->nsm
 // Grid of a tuned kernel over `work` items.
 inline int shape_grid(const hmc_ctx* c, int id, long long work) {
   const Shape& s = c->shape[id];
-  if (s.tiled) {  // blocks of the tiled FP32 CG kernels (their reduction partials)
+  if (s.tiled == 4) work = (work + 1) / 2;  // one work item per pair of cells
+  if (s.tiled && s.tiled != 4) {  // blocks of the tiled FP32 CG kernels (their reduction partials)
     const Geo& g = c->geo;
     return ((g.V + s.threads - 1) / s.threads) * ((g.nt + s.tt - 1) / s.tt);
   }

@@ -396,6 +396,281 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
   ff_write_partial(loc, partB);
 }
 
+// ---------------------------------------------------------------------------
+// The same FP32 CG pair with two cells per thread (n even). A work item is the
+// pair of cells (i, i+1), i even, of one row and time slice: its complex64
+// values are one 16-byte float4 in each vector, and so are the values of its
+// time partners and of its j-neighbours. The i-neighbour inside the pair is
+// the other half of the thread's own float4; only the one across the pair
+// boundary (i-1 for the A rows, i+2 for the B rows) is an 8-byte load. The
+// rows of Eq. ferm_op are formed in the same order as in mdag_pair / m_pair,
+// so the results equal those of the one-cell kernels.
+struct Nbr2 {
+  int q;         // even cell-time index of the pair's first cell (A site)
+  int tm, tp;    // the pair at t-1, t+1 (wrapped)
+  int jm1, jp1;  // the pair at j-1, j+1 (wrapped)
+  int im1;       // the single cell (i-1, j) of the first cell
+  int ip1;       // the single cell (i+2, j) beyond the second cell
+  bool wrap_tm, wrap_tp;
+};
+
+__device__ __forceinline__ Nbr2 neighbours2(const Geo& g, int q2) {
+  Nbr2 b;
+  const int q = 2 * q2;
+  b.q = q;
+  const int t = (int)fdiv((uint32_t)q, g.fV);
+  const int c = q - t * g.V;
+  const int j = (int)fdiv((uint32_t)c, g.fn);
+  const int i = c - j * g.n;
+  b.wrap_tm = (t == 0);
+  b.wrap_tp = (t == g.nt - 1);
+  b.tm = q - g.V + (b.wrap_tm ? g.H : 0);
+  b.tp = q + g.V - (b.wrap_tp ? g.H : 0);
+  b.im1 = q - 1 + (i == 0 ? g.n : 0);
+  b.ip1 = q + 2 - (i + 2 == g.n ? g.n : 0);
+  b.jm1 = q - g.n + (j == 0 ? g.V : 0);
+  b.jp1 = q + g.n - (j == g.m - 1 ? g.V : 0);
+  return b;
+}
+
+__device__ __forceinline__ Cx<float> lo2(const float4& v) { return Cx<float>{v.x, v.y}; }
+__device__ __forceinline__ Cx<float> hi2(const float4& v) { return Cx<float>{v.z, v.w}; }
+__device__ __forceinline__ float4 cat2(Cx<float> a, Cx<float> b) { return make_float4(a.re, a.im, b.re, b.im); }
+__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float norm4(float4 v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
+
+// e^{i phi} of the two cells of the pair at k (phi as float pairs).
+__device__ __forceinline__ void phase2(const float* phi32, int k, Cx<float>& e0, Cx<float>& e1) {
+  const float2 f = *reinterpret_cast<const float2*>(phi32 + k);
+  float x0 = fmaf(-6.28318530717958648f, rintf(f.x * 0.159154943091895336f), f.x);
+  float x1 = fmaf(-6.28318530717958648f, rintf(f.y * 0.159154943091895336f), f.y);
+  float s0, c0, s1, c1;
+  __sincosf(x0, &s0, &c0);
+  __sincosf(x1, &s1, &c1);
+  e0 = Cx<float>{c0, s0};
+  e1 = Cx<float>{c1, s1};
+}
+
+// Time-hop factors of M^dagger at the pair: A rows (hop to t+1, phase of A at
+// t+1, conjugated), B rows (hop to t-1, phase of B at t-1).
+__device__ __forceinline__ void mdag_factors2(const float* phi32, const Nbr2& nb, int H, float dm, Cx<float> (&za)[2],
+                                              Cx<float> (&zb)[2]) {
+  Cx<float> ea0, ea1, eb0, eb1;
+  phase2(phi32, nb.tp, ea0, ea1);
+  phase2(phi32, H + nb.tm, eb0, eb1);
+  za[0] = cneg_if(Cx<float>{ea0.re - dm, -ea0.im}, nb.wrap_tp);
+  za[1] = cneg_if(Cx<float>{ea1.re - dm, -ea1.im}, nb.wrap_tp);
+  zb[0] = cneg_if(Cx<float>{dm - eb0.re, -eb0.im}, nb.wrap_tm);
+  zb[1] = cneg_if(Cx<float>{dm - eb1.re, -eb1.im}, nb.wrap_tm);
+}
+
+// M^dagger of the vector returned by L4 (float4 pairs at even indices) and
+// L1 (single cells), at the pair nb: the A pair into oA, the B pair into oB.
+template <typename L4, typename L1>
+__device__ __forceinline__ void mdag2(int H, const Cx<float> (&za)[2], const Cx<float> (&zb)[2], float dk,
+                                      const Nbr2& nb, L4 ld4, L1 ld1, float4& oA, float4& oB) {
+  const float4 pa = ld4(nb.q), pb = ld4(H + nb.q);
+  const float4 pat = ld4(nb.tp), pbt = ld4(H + nb.tm);
+  const float4 pbj = ld4(H + nb.jm1), paj = ld4(nb.jp1);
+  const Cx<float> pbi = ld1(H + nb.im1), pai = ld1(nb.ip1);
+  const Cx<float> a0 = hopsum(cfma(za[0], lo2(pat), Cx<float>{-pa.x, -pa.y}), dk, lo2(pb), pbi, lo2(pbj));
+  const Cx<float> a1 = hopsum(cfma(za[1], hi2(pat), Cx<float>{-pa.z, -pa.w}), dk, hi2(pb), lo2(pb), hi2(pbj));
+  const Cx<float> b0 = hopsum(cfma(zb[0], lo2(pbt), lo2(pb)), dk, lo2(pa), hi2(pa), lo2(paj));
+  const Cx<float> b1 = hopsum(cfma(zb[1], hi2(pbt), hi2(pb)), dk, hi2(pa), pai, hi2(paj));
+  oA = cat2(a0, a1);
+  oB = cat2(b0, b1);
+}
+
+// M u at the pair nb (phases of the pair's own cells).
+__device__ __forceinline__ void m2(const Geo& g, const float* phi32, float dm, const Nbr2& nb,
+                                   const float4* __restrict__ u, float4& oA, float4& oB) {
+  const int H = g.H;
+  const float dk = g.dkf;
+  const float2* u2 = reinterpret_cast<const float2*>(u);
+  const float4 ua = u[nb.q >> 1], ub = u[(H + nb.q) >> 1];
+  const float4 uat = u[nb.tm >> 1], ubt = u[(H + nb.tp) >> 1];
+  const float4 ubj = u[(H + nb.jm1) >> 1], uaj = u[nb.jp1 >> 1];
+  const float2 ubi2 = u2[H + nb.im1], uai2 = u2[nb.ip1];
+  Cx<float> ea0, ea1, eb0, eb1;
+  phase2(phi32, nb.q, ea0, ea1);
+  phase2(phi32, H + nb.q, eb0, eb1);
+  const Cx<float> za0 = cneg_if(Cx<float>{ea0.re - dm, ea0.im}, nb.wrap_tm);
+  const Cx<float> za1 = cneg_if(Cx<float>{ea1.re - dm, ea1.im}, nb.wrap_tm);
+  const Cx<float> zb0 = cneg_if(Cx<float>{dm - eb0.re, eb0.im}, nb.wrap_tp);
+  const Cx<float> zb1 = cneg_if(Cx<float>{dm - eb1.re, eb1.im}, nb.wrap_tp);
+  const Cx<float> a0 =
+      hopsum(cfma(za0, lo2(uat), Cx<float>{-ua.x, -ua.y}), dk, lo2(ub), Cx<float>{ubi2.x, ubi2.y}, lo2(ubj));
+  const Cx<float> a1 = hopsum(cfma(za1, hi2(uat), Cx<float>{-ua.z, -ua.w}), dk, hi2(ub), lo2(ub), hi2(ubj));
+  const Cx<float> b0 = hopsum(cfma(zb0, lo2(ubt), lo2(ub)), dk, lo2(ua), hi2(ua), lo2(uaj));
+  const Cx<float> b1 = hopsum(cfma(zb1, hi2(ubt), hi2(ub)), dk, hi2(ua), Cx<float>{uai2.x, uai2.y}, hi2(uaj));
+  oA = cat2(a0, a1);
+  oB = cat2(b0, b1);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag2(Geo g, const float* __restrict__ phi32,
+                                                          const float4* __restrict__ r,
+                                                          const float4* __restrict__ pold,
+                                                          float4* __restrict__ pnew, float4* __restrict__ u,
+                                                          CGScal* sc, const float2* __restrict__ partB, int GB,
+                                                          float2* __restrict__ partA) {
+  __shared__ float s_beta;
+  __shared__ int s_exit, s_done;
+  pdl_wait();
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const int first = sc->first;
+  const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
+  const int H = g.H, H2 = g.H >> 1, Hh = g.H >> 1;
+  const int stride = gridDim.x * blockDim.x;
+  const float2* r1 = reinterpret_cast<const float2*>(r);
+  const float2* po1 = reinterpret_cast<const float2*>(pold);
+  int q2 = blockIdx.x * blockDim.x + threadIdx.x;
+  // first item: both stencils, before beta is known
+  const bool have0 = q2 < H2;
+  Nbr2 nb0;
+  float4 mrA{}, mrB{}, mpA{}, mpB{}, r0a{}, r0b{}, p0a{}, p0b{};
+  if (have0) {
+    nb0 = neighbours2(g, q2);
+    Cx<float> za[2], zb[2];
+    mdag_factors2(phi32, nb0, H, dm, za, zb);
+    mdag2(H, za, zb, dk, nb0, [&](int k) { return r[k >> 1]; },
+          [&](int k) { const float2 v = r1[k]; return Cx<float>{v.x, v.y}; }, mrA, mrB);
+    r0a = r[q2];
+    r0b = r[Hh + q2];
+    if (!first) {
+      mdag2(H, za, zb, dk, nb0, [&](int k) { return pold[k >> 1]; },
+            [&](int k) { const float2 v = po1[k]; return Cx<float>{v.x, v.y}; }, mpA, mpB);
+      p0a = pold[q2];
+      p0b = pold[Hh + q2];
+    }
+  }
+  const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
+  if (threadIdx.x == 0) {
+    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
+    int done = CG_RUNNING;
+    if (!isfinite(rr))
+      done = CG_BREAKDOWN;
+    else if (rr <= sc->thresh)
+      done = CG_CONVERGED;
+    else if (sc->iter >= sc->maxit)
+      done = CG_MAXIT;
+    const double beta = first ? 0.0 : rr / sc->rr;
+    s_beta = (float)beta;
+    s_done = done;
+    if (blockIdx.x == 0) {
+      sc->rr_cur = rr;
+      sc->beta = beta;
+      if (done) {
+        sc->rr = rr;
+        sc->done = done;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float beta = s_beta;
+  float loc = 0.f;
+  if (have0) {
+    const float4 pa = axpy4(beta, p0a, r0a), pb = axpy4(beta, p0b, r0b);
+    const float4 oa = axpy4(beta, mpA, mrA), ob = axpy4(beta, mpB, mrB);
+    pnew[q2] = pa;
+    pnew[Hh + q2] = pb;
+    u[q2] = oa;
+    u[Hh + q2] = ob;
+    loc += norm4(oa) + norm4(ob);
+    if (sigma != 0.f) loc += sigma * (norm4(pa) + norm4(pb));
+  }
+  for (q2 += stride; q2 < H2; q2 += stride) {
+    const Nbr2 nb = neighbours2(g, q2);
+    auto P4 = [&](int k) { return axpy4(beta, pold[k >> 1], r[k >> 1]); };
+    auto P1 = [&](int k) {
+      const float2 a = r1[k], b = po1[k];
+      return Cx<float>{fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y)};
+    };
+    Cx<float> za[2], zb[2];
+    mdag_factors2(phi32, nb, H, dm, za, zb);
+    float4 oa, ob;
+    mdag2(H, za, zb, dk, nb, P4, P1, oa, ob);
+    const float4 pa = P4(nb.q), pb = P4(H + nb.q);
+    pnew[q2] = pa;
+    pnew[Hh + q2] = pb;
+    u[q2] = oa;
+    u[Hh + q2] = ob;
+    loc += norm4(oa) + norm4(ob);
+    if (sigma != 0.f) loc += sigma * (norm4(pa) + norm4(pb));
+  }
+  pdl_trigger();
+  ff_write_partial(loc, partA);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_cg32_m2(Geo g, const float* __restrict__ phi32,
+                                                      const float4* __restrict__ u, const float4* __restrict__ p,
+                                                      float4* __restrict__ x, float4* __restrict__ r, CGScal* sc,
+                                                      const float2* __restrict__ partA, int GA,
+                                                      float2* __restrict__ partB) {
+  __shared__ float s_alpha;
+  __shared__ int s_exit, s_bad;
+  pdl_wait();
+  if (threadIdx.x == 0) s_exit = sc->done;
+  __syncthreads();
+  if (s_exit) return;
+  const float dm = sc->dm32, sigma = sc->sigma32;
+  const int H2 = g.H >> 1, Hh = g.H >> 1;
+  const int stride = gridDim.x * blockDim.x;
+  int q2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool have0 = q2 < H2;
+  float4 oA0{}, oB0{};
+  if (have0) m2(g, phi32, dm, neighbours2(g, q2), u, oA0, oB0);
+  const float2 pAp_pair = ff_sum_partials(partA, GA);
+  if (threadIdx.x == 0) {
+    const double pAp = ff_to_double(pAp_pair);
+    const double rr = sc->rr_cur;
+    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+    s_bad = bad;
+    s_alpha = bad ? 0.f : (float)(rr / pAp);
+    if (blockIdx.x == 0) {
+      sc->pAp = pAp;
+      sc->rr = rr;
+      sc->first = 0;
+      if (bad) {
+        sc->alpha = 0.0;
+        sc->done = CG_BREAKDOWN;
+      } else {
+        sc->alpha = rr / pAp;
+        sc->iter += 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float alpha = s_alpha;
+  float loc = 0.f;
+  auto update = [&](int k, float4 Ap) {
+    const float4 pk = p[k];
+    Ap = axpy4(sigma, pk, Ap);
+    x[k] = axpy4(alpha, pk, x[k]);
+    const float4 rk = axpy4(-alpha, Ap, r[k]);
+    r[k] = rk;
+    loc = fmaf(rk.x, rk.x, fmaf(rk.y, rk.y, loc));
+    loc = fmaf(rk.z, rk.z, fmaf(rk.w, rk.w, loc));
+  };
+  if (have0) {
+    update(q2, oA0);
+    update(Hh + q2, oB0);
+  }
+  for (q2 += stride; q2 < H2; q2 += stride) {
+    float4 oA, oB;
+    m2(g, phi32, dm, neighbours2(g, q2), u, oA, oB);
+    update(q2, oA);
+    update(Hh + q2, oB);
+  }
+  pdl_trigger();
+  ff_write_partial(loc, partB);
+}
+
 // True residual b - (M M^dagger + sigma) x and its norm in FP64 (Section 3;
 // the restart step of Algorithm A.1).
 template <typename R>
@@ -787,7 +1062,11 @@ hmc_status cg32_pmdag_launch(hmc_ctx* c, const Geo& g, const float2* r, const fl
   if (sh.tiled == 1 && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
   if (sh.tiled == 2 && !cg32_march_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "CG shape does not fit");
   return launch_b(c, K_CG_MDAG32, 36.0 * g.N, [&] {
-    if (sh.tiled) {
+    if (sh.tiled == 4) {
+      launch_pdl(c, k_cg32_pmdag2, dim3(shape_grid(c, K_CG_MDAG32, g.H)), sh.threads, c->stream, g,
+                 (const float*)c->ws[WS_PHI32], (const float4*)r, (const float4*)pold, (float4*)pnew, (float4*)u, sc,
+                 (const float2*)c->partB, GB, (float2*)c->partA);
+    } else if (sh.tiled) {
       cg32_alt_pmdag(c, g, sh, r, pold, pnew, u, sc, GB);
     } else {
       launch_pdl(c, k_cg32_pmdag, dim3(shape_grid(c, K_CG_MDAG32, g.H)), sh.threads, c->stream, g,
@@ -803,7 +1082,11 @@ hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2
   if (sh.tiled == 1 && !cg32_tiled_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "tiled CG shape does not fit");
   if (sh.tiled == 2 && !cg32_march_ok(c, g, sh.threads, sh.tt)) return fail(c, HMC_ERR_INVALID, "CG shape does not fit");
   return launch_b(c, K_CG_M32, 52.0 * g.N, [&] {
-    if (sh.tiled) {
+    if (sh.tiled == 4) {
+      launch_pdl(c, k_cg32_m2, dim3(shape_grid(c, K_CG_M32, g.H)), sh.threads, c->stream, g,
+                 (const float*)c->ws[WS_PHI32], (const float4*)u, (const float4*)p, (float4*)x, (float4*)r, sc,
+                 (const float2*)c->partA, GA, (float2*)c->partB);
+    } else if (sh.tiled) {
       cg32_alt_m(c, g, sh, u, p, x, r, sc, GA);
     } else {
       launch_pdl(c, k_cg32_m, dim3(shape_grid(c, K_CG_M32, g.H)), sh.threads, c->stream, g, phase_of<float>(c),
@@ -812,10 +1095,12 @@ hmc_status cg32_m_launch(hmc_ctx* c, const Geo& g, const float2* u, const float2
   });
 }
 
-int cg_kernel_occupancy(int id, int threads) {
+int cg_kernel_occupancy(int id, int threads, int pairs) {
   int nb = 0;
   const void* f = nullptr;
-  switch (id) {
+  if (pairs && id == K_CG_MDAG32) f = (const void*)k_cg32_pmdag2;
+  if (pairs && id == K_CG_M32) f = (const void*)k_cg32_m2;
+  if (f == nullptr) switch (id) {
     case K_CG_MDAG64: f = (const void*)k_cg_mdag<double>; break;
     case K_CG_M64: f = (const void*)k_cg_m<double>; break;
     case K_CG_P64: f = (const void*)k_cg_p<double>; break;

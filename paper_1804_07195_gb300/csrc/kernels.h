@@ -86,8 +86,9 @@ hmc_status loop_continue_launch(hmc_ctx* c, cudaGraphConditionalHandle h, const 
 hmc_status cg32_persist_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1,
                                float2* u, CGScal* sc);
 
-// Resident blocks per SM of a CG kernel at `threads` threads per block.
-int cg_kernel_occupancy(int id, int threads);
+// Resident blocks per SM of a CG kernel at `threads` threads per block
+// (pairs: the FP32 kernels with two cells per thread).
+int cg_kernel_occupancy(int id, int threads, int pairs = 0);
 
 // Precision conversions.
 hmc_status to32_launch(hmc_ctx* c, int N, const double2* in, float2* out);

@@ -89,8 +89,9 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
   HMC_CUDA(c, cudaEventCreate(&e1));
   // candidates: {threads, waves, tiled, time slices per tile}
   std::vector<Shape> cands;
-  const bool want_tiled = sizeof(R) == 4 && c->cg32_variant != 1;
-  if (want_tiled && c->cg32_variant != 3)
+  const int var = c->cg32_variant;
+  const bool want_tiled = sizeof(R) == 4 && (var == 0 || var == 2 || var == 3 || var == 4);
+  if (want_tiled && var != 3)
     for (int tc : {256, 512, 1024})
       for (int tt : {2, 4, 8})
         if (cg32_tiled_ok(c, g, tc, tt)) {
@@ -100,7 +101,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           sh.tt = tt;
           cands.push_back(sh);
         }
-  if (want_tiled && c->cg32_variant != 2)
+  if (want_tiled && var != 2)
     for (int th : {128, 256, 512})
       for (int tt : {2, 4, 8})
         if (cg32_march_ok(c, g, th, tt)) {
@@ -111,14 +112,20 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           cands.push_back(sh);
         }
   // variants 2 and 3 keep the grid-stride candidates only where none of theirs fits
-  if (!(sizeof(R) == 4 && c->cg32_variant >= 2 && !cands.empty()))
-    for (int th : {128, 256, 512})
-      for (int wv : {1, 2, 4, 0}) {
-        Shape sh;
-        sh.threads = th;
-        sh.waves = wv;
-        cands.push_back(sh);
-      }
+  // (variant 5, two cells per thread, falls back to variant 1 where n is odd)
+  if (!(sizeof(R) == 4 && var >= 2 && var <= 4 && !cands.empty()))
+    for (int pairs : {0, 1})
+      for (int th : {128, 256, 512})
+        for (int wv : {1, 2, 4, 0}) {
+          const bool pairs_ok = sizeof(R) == 4 && !(g.n & 1);
+          if (pairs && !(pairs_ok && (var == 0 || var == 5))) continue;
+          if (!pairs && sizeof(R) == 4 && var == 5 && pairs_ok) continue;
+          Shape sh;
+          sh.threads = th;
+          sh.waves = wv;
+          sh.tiled = pairs ? 4 : 0;
+          cands.push_back(sh);
+        }
   float best = 1e30f;
   Shape keep[3];
   for (const Shape& cand : cands) {
@@ -126,7 +133,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
       for (int k = 0; k < nk; ++k) {
         Shape& sh = c->shape[ids[k]];
         sh = cand;
-        sh.occ = cand.tiled ? 1 : cg_kernel_occupancy(ids[k], cand.threads);
+        sh.occ = (cand.tiled && cand.tiled != 4) ? 1 : cg_kernel_occupancy(ids[k], cand.threads, cand.tiled == 4);
       }
       // tolerance 0: no candidate stops early
       HMC_TRY(init0_launch<R>(c, g.N, b, x, r, p, sc, 0.0, 1 << 30, sigma, tk, c->delta * ms));

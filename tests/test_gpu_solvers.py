@@ -141,12 +141,13 @@ def test_fcg_mixed(name, ms):
         assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name,ms,sigma,bound", [("L36x36x64", 0.0, 0.0, 1e-3), ("L36x36x64", 0.4, 0.05, 5e-5),
-                                                 ("L102x102x64", 0.1, 0.0, 1e-3), ("L36x36x21", 0.2, 0.0, 1e-4)])
+                                                 ("L102x102x64", 0.1, 0.0, 1e-3), ("L36x36x21", 0.2, 0.0, 1e-4),
+                                                 ("L35x12x16", 0.2, 0.0, 1e-4)])
 def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching,
-    persistent) solve
+    persistent, grid-stride with two cells per thread) solve
     to the single-precision floor, and FGMRES built on them meets 1e-10. The
     FP32 solution's true residual is bounded by the recursive tolerance plus
     the rounding drift, about eps_32 times the condition number (near 10^4 at
@@ -155,7 +156,12 @@ def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     count per block the tiled and marching kernels can take (2, 4, 8), and a
     ragged last block of cells."""
     need_gpu()
-    w = W.small(36, 36, 21, seed=2121, U=3.0, beta=6.0) if name == "L36x36x21" else W.workload(name)
+    if name == "L36x36x21":
+        w = W.small(36, 36, 21, seed=2121, U=3.0, beta=6.0)
+    elif name == "L35x12x16":  # odd n: no cell pairs, variant 5 takes one cell per thread
+        w = W.small(35, 12, 16, seed=3512, U=3.0, beta=6.0)
+    else:
+        w = W.workload(name)
     ol = OLat.from_params(w.lat)
     with ctx_for(w.lat) as ctx:
         ctx.set_cg_variant(variant)
@@ -163,8 +169,10 @@ def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
         shapes = ctx.profile_read()
         x, finfo = ctx.solve_fgmres(dev(w.phi), ms, dev(w.b), sigma=sigma, tol=1e-10, a=1.0)
     waves = shapes["cg_pMdag_f32"]["waves"]
+    design = shapes["cg_pMdag_f32"]["design"]
     persist = shapes["cg_persist_f32"]["launches"]
-    assert {1: waves >= 0, 2: -1000 < waves < 0, 3: waves <= -1000, 4: True}[variant]
+    assert {1: waves >= 0 and design == 0, 2: -1000 < waves < 0, 3: waves <= -1000, 4: True,
+            5: waves >= 0 and design == (4 if w.lat.n % 2 == 0 else 0)}[variant]
     assert (persist > 0) == (variant == 4)
     b32 = w.b.astype(np.complex64).astype(np.complex128)
     assert info["iters"] > 0 and info["status"] == 0
@@ -187,3 +195,29 @@ def test_solves_run_as_one_graph_launch_with_a_device_loop():
         x3, i3 = ctx.solve_cg(dev(w.phi), 0.3, dev(w.b), tol=1e-10)
     assert i1["iters"] == i2["iters"] == i3["iters"]
     assert np.array_equal(host(x1), host(x2)) and np.array_equal(host(x1), host(x3))
+
+
+def test_spcg_two_cell_kernels_with_an_unaligned_solution_vector():
+    """The two-cells-per-thread FP32 CG kernels access x in 16-byte units; a
+    caller's x that is only 8-byte aligned is solved in a workspace vector and
+    copied, with the same iterates as an aligned x."""
+    need_gpu()
+    w = W.small(12, 12, 32, seed=1212, U=3.0, beta=6.0)
+    N = w.lat.nsites
+    ol = OLat.from_params(w.lat)
+    import paper_1804_07195_gb300 as hmc
+    from paper_1804_07195_gb300 import _abi
+    import ctypes as C
+    b32 = dev(w.b.astype(np.complex64))
+    with ctx_for(w.lat) as ctx:
+        ctx.set_cg_variant(5)
+        xa, ia = ctx.solve_spcg(dev(w.phi), 0.1, b32, tol=1e-5, maxit=5000)
+        buf = torch.zeros(N + 1, dtype=torch.complex64, device="cuda")
+        info = _abi.hmc_solve_info()
+        st = ctx.lib.hmc_solve_spcg(ctx.h, C.c_void_p(dev(w.phi).data_ptr()), 0.1, 0.0, C.c_void_p(b32.data_ptr()),
+                                    C.c_void_p(buf[1:].data_ptr()), 1e-5, 5000, C.byref(info))
+        torch.cuda.synchronize()
+        assert st == 0 and ctx.profile_read()["cg_pMdag_f32"]["design"] == 4
+    assert info.iters == ia["iters"]
+    assert np.array_equal(host(buf[1:]), host(xa))
+    assert true_rel(ol, w.phi, 0.1, 0.0, host(buf[1:]).astype(np.complex128), w.b.astype(np.complex64).astype(np.complex128)) < 1e-4

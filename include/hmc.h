@@ -269,6 +269,32 @@ hmc_status hmc_md_trajectory(hmc_ctx* ctx, double* phi, double* pi, int nmass,
                              const hmc_solver_opts* action_opts, double* H0, double* H1,
                              hmc_solve_info* agg);
 
+/* One Markov chain of a batched trajectory: its lattice (chains may differ in
+ * size and couplings), its field phi and momenta pi (device, N doubles each,
+ * updated in place) and its nmass+1 heat-bath vectors rho (device pointers to
+ * complex128 vectors). */
+typedef struct {
+  hmc_lattice lat;
+  double* phi;
+  double* pi;
+  const void* const* rho;
+} hmc_chain;
+
+/* One MD trajectory for each of nchains independent chains, advanced in
+ * lockstep (Section 2's HMC outline, the integrators of Sections 4 and 5.2, the
+ * Hasenbusch terms of Section 5.1 with the same masses for every chain): the
+ * same steps as hmc_md_trajectory for each chain, but every solve the chains
+ * need at one point of the schedule -- one per chain and term -- runs as one
+ * batched solve (hmc_solve_batched; FP64 CG for HMC_SOLVER_CG64, else FP32 CG
+ * under FP64 defect correction to the options' tolerance). H0, H1 and infos
+ * (may be NULL) receive nchains entries. The context keeps one internal context
+ * per chain (recreated when that chain's lattice changes), freed by
+ * hmc_destroy. Synchronous. */
+hmc_status hmc_md_trajectory_batched(hmc_ctx* ctx, int nchains, const hmc_chain* chains, int nmass,
+                                     const double* masses, const hmc_integrator* integ,
+                                     const hmc_solver_opts* md_opts, const hmc_solver_opts* action_opts,
+                                     double* H0, double* H1, hmc_solve_info* infos);
+
 /* ---- launch shapes and graphs ----------------------------------------------- */
 
 /* The calls of this section and the next choose or report how the library

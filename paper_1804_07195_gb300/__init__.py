@@ -276,6 +276,31 @@ class Context:
             C.byref(action_opts.c()), C.byref(H0), C.byref(H1), C.byref(info)))
         return H0.value, H1.value, info.as_dict()
 
+    def md_trajectory_batched(self, chains: List[dict], masses, integ: Integrator, md_opts: SolverOpts,
+                              action_opts: SolverOpts):
+        """One trajectory for each chain (dicts with lattice, phi, pi, rho), all
+        advanced in lockstep with batched solves; phi and pi are updated in
+        place. Returns (H0 list, H1 list, info list)."""
+        import torch
+        K = len(chains)
+        arr = (_abi.hmc_chain * K)()
+        keep = []
+        for k, ch in enumerate(chains):
+            lat = ch["lattice"]
+            n = lat.nsites
+            rho = (C.c_void_p * len(ch["rho"]))(*[_ptr(r, torch.complex128, n, "rho").value for r in ch["rho"]])
+            keep.append(rho)
+            arr[k] = _abi.hmc_chain(lat.c(), _ptr(ch["phi"], torch.float64, n, "phi"),
+                                    _ptr(ch["pi"], torch.float64, n, "pi"), rho)
+        m = (C.c_double * max(1, len(masses)))(*masses)
+        H0 = (C.c_double * K)()
+        H1 = (C.c_double * K)()
+        infos = (_abi.hmc_solve_info * K)()
+        self._check(self.lib.hmc_md_trajectory_batched(self.h, K, arr, len(masses), m, C.byref(integ.c()),
+                                                       C.byref(md_opts.c()), C.byref(action_opts.c()), H0, H1,
+                                                       infos))
+        return list(H0), list(H1), [i.as_dict() for i in infos]
+
     def solve_batched(self, systems: List[dict], mixed: bool = True):
         """systems: dicts with lattice (Lattice), phi, ms, sigma, b, x, tol, maxit."""
         import torch

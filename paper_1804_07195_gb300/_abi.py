@@ -63,6 +63,10 @@ class hmc_system(C.Structure):
                 ("tol", C.c_double), ("maxit", C.c_int)]
 
 
+class hmc_chain(C.Structure):
+    _fields_ = [("lat", hmc_lattice), ("phi", C.c_void_p), ("pi", C.c_void_p), ("rho", C.POINTER(C.c_void_p))]
+
+
 class hmc_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("ms_total", C.c_double),
                 ("bytes_total", C.c_double), ("threads", C.c_int), ("waves", C.c_int), ("design", C.c_int)]
@@ -102,6 +106,9 @@ PROTOTYPES = {
     "hmc_md_trajectory": (S, [P, P, P, I, C.POINTER(D), C.POINTER(P), C.POINTER(hmc_integrator),
                               C.POINTER(hmc_solver_opts), C.POINTER(hmc_solver_opts),
                               C.POINTER(D), C.POINTER(D), C.POINTER(hmc_solve_info)]),
+    "hmc_md_trajectory_batched": (S, [P, I, C.POINTER(hmc_chain), I, C.POINTER(D), C.POINTER(hmc_integrator),
+                                      C.POINTER(hmc_solver_opts), C.POINTER(hmc_solver_opts), C.POINTER(D),
+                                      C.POINTER(D), C.POINTER(hmc_solve_info)]),
     "hmc_set_cg_variant": (S, [P, I]),
     "hmc_set_apply_variant": (S, [P, I]),
     "hmc_apply_variant": (S, [P, I, C.POINTER(I)]),

@@ -371,6 +371,9 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
 
 hmc_status hmc_destroy(hmc_ctx* c) {
   if (!c) return HMC_ERR_INVALID;
+  for (hmc_ctx* sc : c->subs)
+    if (sc) hmc_destroy(sc);
+  c->subs.clear();
   if (c->stream || c->device >= 0) cudaStreamSynchronize(c->stream);
   destroy_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -164,6 +164,10 @@ struct hmc_ctx {
   int bar_extra = 0;         // test hook: extra arrivals every grid barrier waits for
   long long bar_limit = 0;   // test hook: barrier wait limit in SM cycles (0: default)
 
+  // per-chain contexts of hmc_md_trajectory_batched (slot i: chain i of the
+  // last call; recreated when a chain's lattice changes), destroyed with ctx
+  std::vector<hmc_ctx*> subs;
+
   bool use_graphs = true;
   bool use_loop_graphs = true;   // whole solves as one graph with a device-side while loop
   unsigned* loop_trips = nullptr;       // device: [0] trips of the loop so far, [1] bound

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "force.h"
+#include "integrator.h"
 
 namespace hmc {
 
@@ -31,6 +32,7 @@ struct MD {
   SolveStats st;
   int nforce = 0;
   hmc_status err = HMC_OK;
+  double* phit = nullptr;  // force-gradient: the displaced field
 
   size_t N() const { return (size_t)c->geo.N; }
 
@@ -81,51 +83,33 @@ struct MD {
     double* f = ensure(k);
     if (f) err = axpy_real_launch(c, (int)N(), -coef, f, pi);
   }
-};
 
-// Nested Omelyan (Section 5.2) over levels with steps[k] steps per trajectory.
-struct Nested {
-  MD& md;
-  std::vector<int> ratio;
-  int L;
-  double zeta;
+  bool ok() const { return err == HMC_OK; }
 
-  void inner_first(int k, double h) {
-    if (k == L - 1) {
-      md.Q(0.5 * h);
+  // The middle kick of the force-gradient integrator (Eq. force_cal): the
+  // force at phi_tilde = phi - (h^2/24) dS/dphi(phi) (new field versions, so
+  // that neither the tables nor the cache of one field serve the other).
+  void fg_kick(double coef, double h) {
+    if (err != HMC_OK) return;
+    const double* g1 = ensure(-1);
+    if (!g1) return;
+    if (!phit) {
+      err = ws_get(c, WS_MD_PHI0, sizeof(double) * N(), (void**)&phit);
+      if (err != HMC_OK) return;
+    }
+    cudaError_t e = cudaMemcpyAsync(phit, phi, sizeof(double) * N(), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+      err = cuda_fail(c, e, "force-gradient copy");
       return;
     }
-    const int r = ratio[k + 1];
-    const double hh = h / r;
-    for (int i = 0; i < r / 2; ++i) step(k + 1, hh);
-    if (r % 2) half_first(k + 1, hh);
-  }
-  void inner_second(int k, double h) {
-    if (k == L - 1) {
-      md.Q(0.5 * h);
-      return;
-    }
-    const int r = ratio[k + 1];
-    const double hh = h / r;
-    if (r % 2) half_second(k + 1, hh);
-    for (int i = 0; i < r / 2; ++i) step(k + 1, hh);
-  }
-  void step(int k, double h) {
-    md.P(k, zeta * h);
-    inner_first(k, h);
-    md.P(k, (1.0 - 2.0 * zeta) * h);
-    inner_second(k, h);
-    md.P(k, zeta * h);
-  }
-  void half_first(int k, double h) {
-    md.P(k, zeta * h);
-    inner_first(k, h);
-    md.P(k, 0.5 * (1.0 - 2.0 * zeta) * h);
-  }
-  void half_second(int k, double h) {
-    md.P(k, 0.5 * (1.0 - 2.0 * zeta) * h);
-    inner_second(k, h);
-    md.P(k, zeta * h);
+    err = axpy_real_launch(c, (int)N(), -(h * h / 24.0), g1, phit);
+    if (err != HMC_OK) return;
+    double* keep = phi;
+    phi = phit;
+    ++ver;
+    P(-1, coef);
+    phi = keep;
+    ++ver;
   }
 };
 
@@ -190,44 +174,7 @@ extern "C" hmc_status hmc_md_trajectory(hmc_ctx* c, double* phi, double* pi, int
   for (int i = 0; i <= nmass; ++i) h0 += c->dscal_host[56 + i];
 
   // molecular dynamics
-  const double tau = integ->tau;
-  if (integ->kind == HMC_INTEG_NESTED_OMELYAN) {
-    Nested nest{md, {}, (int)steps.size(), integ->zeta};
-    nest.ratio.push_back(steps[0]);
-    for (size_t k = 1; k < steps.size(); ++k) nest.ratio.push_back(steps[k] / steps[k - 1]);
-    const double h0s = tau / steps[0];
-    for (int i = 0; i < steps[0] && md.err == HMC_OK; ++i) nest.step(0, h0s);
-  } else if (integ->kind == HMC_INTEG_LEAPFROG) {
-    const double h = tau / integ->nmd;
-    for (int i = 0; i < integ->nmd && md.err == HMC_OK; ++i) {
-      md.Q(0.5 * h);
-      md.P(-1, h);
-      md.Q(0.5 * h);
-    }
-  } else {
-    // force gradient, Eq. force_cal: the middle kick uses the force at
-    // phi_tilde = phi - (h^2/24) dS/dphi(phi)
-    const double h = tau / integ->nmd;
-    double* phit;
-    HMC_TRY(ws_get(c, WS_MD_PHI0, sizeof(double) * N, (void**)&phit));
-    for (int i = 0; i < integ->nmd && md.err == HMC_OK; ++i) {
-      md.P(-1, h / 6.0);
-      md.Q(0.5 * h);
-      const double* g1 = md.ensure(-1);
-      if (!g1) break;
-      HMC_CUDA(c, cudaMemcpyAsync(phit, phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
-      HMC_TRY(axpy_real_launch(c, (int)N, -(h * h / 24.0), g1, phit));
-      // kick with the force at phi_tilde, then return to phi (new versions so
-      // that neither the tables nor the cache of one field serve the other)
-      md.phi = phit;
-      ++md.ver;
-      md.P(-1, (2.0 / 3.0) * h);
-      md.phi = phi;
-      ++md.ver;
-      md.Q(0.5 * h);
-      md.P(-1, h / 6.0);
-    }
-  }
+  run_integrator(md, integ->kind, steps, integ->nmd, integ->zeta, integ->tau);
   if (md.err != HMC_OK) return md.err;
 
   // H1 = S(phi') + pi'^2/2 with the action solves at action_opts' tolerance

@@ -154,6 +154,47 @@ def cpu_oracle_cg(iters: int):
     return 1e3 * dt / max(res.iters, 1), res.iters
 
 
+def _c3_oracle_job(q):
+    """(In a spawned process) the oracle's FP64 CG on the 36x36x64 system
+    (m_s = 0) to 1e-12, timed."""
+    import workloads as W
+    from oracle import fermion, solvers
+    from oracle.lattice import Lattice
+    w = W.workload("L36x36x64")
+    lat = Lattice.from_params(w.lat)
+    A = lambda v: fermion.apply_MMdag(lat, w.phi, 0.0, v)
+    t0 = time.perf_counter()
+    res = solvers.cg(A, w.b, tol=1e-12, maxit=100000)
+    dt = time.perf_counter() - t0
+    q.put({"x": res.x, "s": dt, "iters": res.iters, "true_rel_res": solvers.true_rel_residual(A, res.x, w.b)})
+
+
+def start_c3_oracle():
+    """Start the 36x36x64 oracle solve in a spawned process (one host core)
+    so that it runs beside the GPU measurements that follow the timed region."""
+    import multiprocessing as mp
+    mctx = mp.get_context("spawn")
+    q = mctx.Queue()
+    proc = mctx.Process(target=_c3_oracle_job, args=(q,), daemon=True)
+    proc.start()
+    return proc, q
+
+
+def cpu_oracle_c3(job, sols):
+    """The oracle's FP64 CG solution of the 36x36x64 system (1e-12) and the
+    relative error of each GPU solution against it."""
+    proc, q = job
+    r = q.get(timeout=1800)
+    proc.join(60)
+    xr = r["x"]
+    nr = float(np.linalg.norm(xr))
+    return {"oracle_fp64_cg_s": r["s"], "oracle_iters": r["iters"], "oracle_tol": 1e-12,
+            "oracle_true_rel_res": r["true_rel_res"], "cores": 1,
+            "rel_error": {k: float(np.linalg.norm(x - xr) / nr) for k, x in sols.items()},
+            "note": "run in a spawned process on one host core while the GPU measurements after the timed "
+                    "region ran"}
+
+
 def run_reference(args, rank):
     """Reference arm: the CPU oracle (numpy, complex128) as it stands, each step
     a bounded sample of the same workload: oracle M M^dagger applications on
@@ -205,8 +246,9 @@ def main():
                     help="2 = each CG solve one graph launch with a device-side loop (default); 1 = graph "
                          "chunks with host checks, the mode kernel profilers can see into")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "mmdag32_stream",
-                             "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64", "batched"],
+                    choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs",
+                             "mmdag32_stream", "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64",
+                             "batched", "force", "md_short"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
@@ -303,6 +345,7 @@ def main():
     if dist is not None:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    c3_job = start_c3_oracle() if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None
     total_ms = float(sum(step_ms))
     launches = ctx.profile_read()
     gpu_launches = int(sum(v["launches"] for v in launches.values()))
@@ -375,7 +418,8 @@ def main():
     # iterations of single-precision CG (no convergence test reached)
     designs = {}
     with hmc.Context(lat) as c2:
-        for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3), ("persistent", 4)):
+        for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3), ("persistent", 4),
+                         ("grid_stride_two_cells", 5)):
             c2.set_cg_variant(v)
             b32 = b.to(torch.complex64)
             c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
@@ -389,7 +433,7 @@ def main():
             sh = c2.profile_read()["cg_M_update_f32"]
             designs[vname] = {"ms": a.elapsed_time(z), "iters": info["iters"],
                               "us_per_iter": 1e3 * a.elapsed_time(z) / max(info["iters"], 1),
-                              "shape": {"threads": sh["threads"], "waves": sh["waves"]}}
+                              "shape": {"threads": sh["threads"], "waves": sh["waves"], "design": sh["design"]}}
     solve["fp32_cg_designs"] = designs
     # the pair as production runs it (graph replay, no per-launch events): one
     # FP32 CG iteration moves 36 + 52 = 88 algorithmic bytes per site
@@ -406,7 +450,25 @@ def main():
     # the batched workload: 48 uneven lattices x 3 masses = 144 systems at 1e-10,
     # batched mixed vs batched FP64 vs FP64 CG one system at a time
     solve["batched_48_lattices"] = batched_solve_times(hmc, W, torch, stream, flush)
+    solve["batched_trajectory_48_chains"] = batched_trajectory_times(hmc, W, torch, stream, flush)
+    solve["c3_36x36x64"], c3_sols = c3_solves(hmc, W, torch, stream, flush)
     solve["apply"] = apply_rates(hmc, W, torch, stream, flush, hbm)
+
+    # the first timed step's trajectory once more with FP64 solves at the same
+    # tolerances (forces 1e-10, action 1e-12): dH of the mixed-precision path
+    # against FP64 at the bench's own settings
+    fp64_md = hmc.SolverOpts(method=0, tol=1e-10)
+    fp64_act = hmc.SolverOpts(method=0, tol=1e-12)
+    pi_s, rho_s = dev_inputs[args.warmup]
+    phi_f = phi0.clone()
+    H0f, H1f, info_f = ctx.md_trajectory(phi_f, pi_s.clone(), masses, rho_s, integ, fp64_md, fp64_act)
+    dH_check = {"dH_mixed": float(dH[0]), "dH_fp64": H1f - H0f, "abs_difference": abs(H1f - H0f - dH[0]),
+                "action_true_rel_res_fp64": info_f["true_rel_res"],
+                "settings": "both runs: forces from solves at 1e-10, actions at 1e-12 (mixed: FGMRES with FP32 CG "
+                            "inner solves; FP64: CG); the same phi, pi and rho",
+                "note": "the difference is set by the solver tolerance of the MD forces (different rounding of "
+                        "forces at 1e-10 moves the trajectory), not by the operator kernels; at solves of 1e-15 "
+                        "the two agree within 1e-8 (tests/test_gpu_md.py)"}
 
     # end to end through the public API with host buffers
     e2e_val = None
@@ -438,11 +500,14 @@ def main():
     ctx.close()
 
     cpu = None
-    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
+    if c3_job is not None:
         v, reps, dt = cpu_oracle_apply(args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"numpy complex128 oracle M M^dagger on the same 1,331,712-site lattice, "
                          f"{reps} applications in {dt:.1f} s (single-threaded numpy)"}
+        c3 = cpu_oracle_c3(c3_job, c3_sols)
+        cpu["c3"] = c3
+        solve["c3_36x36x64"]["error_vs_oracle_fp64_cg"] = c3["rel_error"]
         cg_ms, cg_it = cpu_oracle_cg(6)
         gpu_cg = solve["fp64_cg"]
         cpu["cg"] = {"iterations_timed": cg_it, "ms_per_iteration": cg_ms,
@@ -462,7 +527,8 @@ def main():
                            "cg_graph_mode": {2: "device-side loop, one graph launch per solve",
                                              1: "graph chunks with host checks",
                                              0: "direct launches"}[graph_mode],
-                           "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall},
+                           "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall,
+                           "dH_mixed_vs_fp64": dH_check},
                 "roofline": roofline, "roofline_pair_graph_replay": pair, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -573,21 +639,132 @@ def batched_solve_times(hmc, W, torch, stream, flush):
         return worst
 
     out = {"systems": len(systems), "sites": int(sum(sy["lattice"].nsites for sy in systems))}
+
+    def site_applies(infos):
+        # sites x M M^dagger applications summed over the systems (both precisions)
+        return float(sum(sy["lattice"].nsites * (i["applies64"] + i["applies32"]) for sy, i in zip(systems, infos)))
+
     ms, infos = timed(lambda: any_ctx.solve_batched(systems, mixed=True))
     out["batched_mixed_ms"] = ms
     out["batched_mixed_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)
+    out["batched_mixed_gsite_s"] = site_applies(infos) / (ms * 1e-3) / 1e9
     ms, infos = timed(lambda: any_ctx.solve_batched(systems, mixed=False))
     out["batched_fp64_ms"] = ms
     out["batched_fp64_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)
+    out["batched_fp64_gsite_s"] = site_applies(infos) / (ms * 1e-3) / 1e9
     ms, worst = timed(lambda: seq("cg"))
     out["sequential_fp64_cg_ms"] = ms
     out["sequential_fp64_cg_max_true_rel_res"] = worst
     ms, worst = timed(lambda: seq("fgmres"))
     out["sequential_mixed_fgmres_ms"] = ms
     out["speedup_batched_mixed_vs_sequential_fp64"] = out["sequential_fp64_cg_ms"] / out["batched_mixed_ms"]
+    out["note"] = ("gsite_s = sum over systems of sites x M M^dagger applications (FP64 and FP32) / time: "
+                   "the operator throughput the batched solve sustains")
     for c in ctxs.values():
         c.close()
     return out
+
+
+def batched_trajectory_times(hmc, W, torch, stream, flush):
+    """The 48 batched instances run as independent Markov chains: one nested
+    Omelyan trajectory per chain (3 Hasenbusch masses, N_MD and time scales of
+    workloads.BATCH_NMD / BATCH_NI, mixed-precision solves at 1e-10 for the
+    forces and 1e-12 for the action), all chains in lockstep with every
+    schedule point's solves batched (hmc_md_trajectory_batched), against the
+    same trajectories one chain at a time (hmc_md_trajectory)."""
+    insts = W.batch_instances()
+    extra = W.batch_chains(insts)
+    masses = list(W.BATCH_MASSES)
+    integ = hmc.Integrator(0, W.BATCH_NMD, W.BATCH_NI)
+    md = hmc.SolverOpts(method=1, tol=1e-10, a=1.0)
+    act = hmc.SolverOpts(method=1, tol=1e-12, a=1.0)
+    lats = [hmc.Lattice(w.lat.n, w.lat.m, w.lat.nt, w.lat.kappa, w.lat.U, w.lat.beta) for w in insts]
+    phis = [torch.tensor(w.phi, device="cuda") for w in insts]
+    pis = [torch.tensor(pi, device="cuda") for pi, _ in extra]
+    rhos = [[torch.tensor(r, device="cuda") for r in rho] for _, rho in extra]
+
+    def chains():
+        return [{"lattice": L, "phi": ph.clone(), "pi": pi.clone(), "rho": rh}
+                for L, ph, pi, rh in zip(lats, phis, pis, rhos)]
+
+    out = {"chains": len(insts), "sites": int(sum(L.nsites for L in lats)), "masses": masses,
+           "nmd": W.BATCH_NMD, "time_scales": list(W.BATCH_NI)}
+    with hmc.Context(lats[0]) as ctx:
+        ctx.md_trajectory_batched(chains(), masses, integ, md, act)  # warm (contexts, tuning, graphs)
+        ch = chains()
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        H0, H1, infos = ctx.md_trajectory_batched(ch, masses, integ, md, act)
+        z.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(z)
+    work = float(sum(L.nsites * (i["applies64"] + i["applies32"]) for L, i in zip(lats, infos)))
+    out["batched_ms"] = ms
+    out["batched_gsite_s"] = work / (ms * 1e-3) / 1e9
+    out["dH"] = [h1 - h0 for h0, h1 in zip(H0, H1)]
+    ctxs = {}
+    for L in lats:
+        key = (L.n, L.m, L.nt)
+        if key not in ctxs:
+            ctxs[key] = hmc.Context(L)
+
+    def seq():
+        res = []
+        for L, c in zip(lats, chains()):
+            res.append(ctxs[(L.n, L.m, L.nt)].md_trajectory(c["phi"], c["pi"], masses, c["rho"], integ, md, act))
+        return res
+
+    seq()  # warm
+    flush.zero_()
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    res = seq()
+    z.record(stream)
+    torch.cuda.synchronize()
+    out["sequential_ms"] = a.elapsed_time(z)
+    work_seq = float(sum(L.nsites * (r[2]["applies64"] + r[2]["applies32"]) for L, r in zip(lats, res)))
+    out["sequential_gsite_s"] = work_seq / (out["sequential_ms"] * 1e-3) / 1e9
+    out["speedup_batched_vs_sequential"] = out["sequential_ms"] / out["batched_ms"]
+    out["max_abs_dH_difference_batched_vs_sequential"] = max(
+        abs((r[1] - r[0]) - d) for r, d in zip(res, out["dH"]))
+    for c in ctxs.values():
+        c.close()
+    return out
+
+
+def c3_solves(hmc, W, torch, stream, flush):
+    """The 36x36x64 lattice (m_s = 0, b of the workload, true residual 1e-10):
+    plain FP64 CG and mixed-precision FGMRES (FP32 CG inner solves, FP64
+    outer) at a = 5 (the paper's value) and a = 1, with their iteration counts
+    and times; the solutions are returned for the comparison with the oracle's
+    FP64 CG solution in the CPU-baseline leg."""
+    w = W.workload("L36x36x64")
+    p = w.lat
+    lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+    phi = torch.tensor(w.phi, device="cuda")
+    b = torch.tensor(w.b, device="cuda")
+    out, sols = {"lattice": "36x36x64", "sites": lat.nsites, "ms": 0.0, "tol": 1e-10}, {}
+    with hmc.Context(lat) as ctx:
+        for name, fn in (("fp64_cg", lambda: ctx.solve_cg(phi, 0.0, b, tol=1e-10)),
+                         ("mixed_fgmres_a5", lambda: ctx.solve_fgmres(phi, 0.0, b, tol=1e-10, a=5.0)),
+                         ("mixed_fgmres_a1", lambda: ctx.solve_fgmres(phi, 0.0, b, tol=1e-10, a=1.0))):
+            fn()
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x, info = fn()
+            z.record(stream)
+            torch.cuda.synchronize()
+            out[name] = {"ms": a.elapsed_time(z), "iters": info["iters"], "restarts": info["iters_outer"],
+                         "inner_iters": info["iters_inner"], "true_rel_res": info["true_rel_res"]}
+            sols[name] = x.cpu().numpy()
+    del out["ms"]
+    out["speedup_mixed_a1_vs_fp64"] = out["fp64_cg"]["ms"] / out["mixed_fgmres_a1"]["ms"]
+    return out, sols
 
 
 def replica_seed(base, rank, step):
@@ -659,14 +836,31 @@ def kernel_case(case, graph_mode=2):
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
         ctx.set_graph_mode(graph_mode)
-        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist"):
+        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs"):
             ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
-                                "spcg_persist": 4}[case])
+                                "spcg_persist": 4, "spcg_pairs": 5}[case])
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)
         elif case == "fgmres":
             _, info = ctx.solve_fgmres(phi, 0.0, b, tol=1e-10)
+        elif case == "force":
+            # the benchmark's force of all terms: pseudofermions for the three
+            # masses, then dS/dphi (Gaussian + every Hasenbusch term)
+            masses = list(W.L102_MASSES)
+            rho = [torch.tensor(r, device="cuda") for r in w.rho]
+            opts = hmc.SolverOpts(method=1, tol=1e-10, a=1.0)
+            chis, _ = ctx.make_chi(phi, masses, rho, opts=opts)
+            _, info = ctx.force(phi, masses, chis, opts=opts)
+        elif case == "md_short":
+            # a short trajectory of the benchmark's kind (N_MD = 6, time scales 2, 1, 1):
+            # the MD updates, energies and forces of the path
+            masses = list(W.L102_MASSES)
+            rho = [torch.tensor(r, device="cuda") for r in w.rho]
+            opts = hmc.SolverOpts(method=1, tol=1e-10, a=1.0)
+            H0, H1, info = ctx.md_trajectory(phi.clone(), torch.tensor(w.pi, device="cuda"), masses, rho,
+                                             hmc.Integrator(0, 6, (2, 1, 1)), opts,
+                                             hmc.SolverOpts(method=1, tol=1e-12, a=1.0))
         else:
             x = b.to(torch.complex64) if case == "mmdag32" else b
             ctx.load_field(phi)

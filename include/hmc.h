@@ -322,6 +322,18 @@ hmc_status hmc_md_trajectory_batched(hmc_ctx* ctx, int nchains, const hmc_chain*
  * next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
+/* The FP32 CG of hmc_solve_batched (mixed = 1) runs in one of two designs:
+ * 1 = a captured graph whose device-side loop repeats chunks of per-iteration
+ * kernels (two launches per iteration over all systems); 2 = one persistent
+ * cooperative launch per inner solve, whose blocks walk the systems' blocks
+ * and separate the halves of an iteration by grid barriers (bounded waits: a
+ * wait that gives up returns HMC_ERR_TIMEOUT). variant 0 (default) runs the
+ * first inner solve of the context with 1 and the second with 2 and keeps the
+ * one with the shorter time per iteration; 1 or 2 pins one. The variant in
+ * use (0 = not chosen yet) is reported by hmc_batched_variant. */
+hmc_status hmc_set_batched_variant(hmc_ctx* ctx, int variant);
+hmc_status hmc_batched_variant(hmc_ctx* ctx, int* variant);
+
 /* M M^dagger applications (hmc_apply_MMdag) run in one of two designs:
  * 1 = two passes, u = M^dagger in written to and read back from memory, then
  * M u + sigma in; 2 = one fused kernel: each block stages the time slices of a

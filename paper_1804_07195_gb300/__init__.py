@@ -321,6 +321,16 @@ class Context:
         3: marching; 4: persistent (one cooperative launch per solve)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
+    def set_batched_variant(self, variant: int):
+        """FP32 CG of the batched solve: 0 = choose by timing (default), 1 =
+        graph loop of per-iteration kernels, 2 = one persistent launch."""
+        self._check(self.lib.hmc_set_batched_variant(self.h, variant))
+
+    def batched_variant(self) -> int:
+        v = C.c_int()
+        self._check(self.lib.hmc_batched_variant(self.h, C.byref(v)))
+        return v.value
+
     def set_apply_variant(self, variant: int):
         """M M^dagger applications: 0 = choose by timing (default), 1 = two
         passes through memory, 2 = the fused kernel (u kept on chip)."""

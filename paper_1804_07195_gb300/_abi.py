@@ -110,6 +110,8 @@ PROTOTYPES = {
                                       C.POINTER(hmc_solver_opts), C.POINTER(hmc_solver_opts), C.POINTER(D),
                                       C.POINTER(D), C.POINTER(hmc_solve_info)]),
     "hmc_set_cg_variant": (S, [P, I]),
+    "hmc_set_batched_variant": (S, [P, I]),
+    "hmc_batched_variant": (S, [P, C.POINTER(I)]),
     "hmc_set_apply_variant": (S, [P, I]),
     "hmc_apply_variant": (S, [P, I, C.POINTER(I)]),
     "hmc_set_fused_tile": (S, [P, I, I, I, I, I, I]),

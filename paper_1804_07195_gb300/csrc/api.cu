@@ -9,6 +9,7 @@
 #include <string>
 
 #include "solvers.h"
+#include "trace.h"
 #include "validate.h"
 
 using namespace hmc;
@@ -420,6 +421,7 @@ hmc_status hmc_load_field(hmc_ctx* c, const double* phi) {
 
 hmc_status hmc_apply_M(hmc_ctx* c, const double* phi, double ms, const void* in, void* out, int prec) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_apply_M");
   HMC_TRY(check_prec(c, prec));
   HMC_TRY(check_vec(c, in, prec, "in"));
   HMC_TRY(check_vec(c, out, prec, "out"));
@@ -433,6 +435,7 @@ hmc_status hmc_apply_M(hmc_ctx* c, const double* phi, double ms, const void* in,
 
 hmc_status hmc_apply_Mdag(hmc_ctx* c, const double* phi, double ms, const void* in, void* out, int prec) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_apply_Mdag");
   HMC_TRY(check_prec(c, prec));
   HMC_TRY(check_vec(c, in, prec, "in"));
   HMC_TRY(check_vec(c, out, prec, "out"));
@@ -446,6 +449,7 @@ hmc_status hmc_apply_Mdag(hmc_ctx* c, const double* phi, double ms, const void* 
 hmc_status hmc_apply_MMdag(hmc_ctx* c, const double* phi, double ms, double sigma, const void* in,
                            void* out, int prec) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_apply_MMdag");
   HMC_TRY(check_prec(c, prec));
   HMC_TRY(check_vec(c, in, prec, "in"));
   HMC_TRY(check_vec(c, out, prec, "out"));
@@ -493,6 +497,7 @@ static void fill_info(hmc_solve_info* info, const SolveStats& s, hmc_status st, 
 hmc_status hmc_solve_cg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
                         double tol, int maxit, hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_solve_cg");
   const double t0 = now_s();
   HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
   HMC_TRY(prepare_field(c, phi));
@@ -505,6 +510,7 @@ hmc_status hmc_solve_cg(hmc_ctx* c, const double* phi, double ms, double sigma, 
 hmc_status hmc_solve_spcg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
                           double tol, int maxit, hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_solve_spcg");
   const double t0 = now_s();
   HMC_TRY(solve_checks(c, ms, sigma, b, x, 32, tol, maxit));
   HMC_TRY(prepare_field(c, phi));
@@ -524,6 +530,7 @@ hmc_status hmc_solve_fgmres(hmc_ctx* c, const double* phi, double ms, double sig
                             double tol, int restart, double a, int inner_prec, int maxit,
                             hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_solve_fgmres");
   const double t0 = now_s();
   HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
   if (restart < 1 || restart > kMaxRestart) return fail(c, HMC_ERR_INVALID, "restart must be in [1, 16]");
@@ -540,6 +547,7 @@ hmc_status hmc_solve_fgmres(hmc_ctx* c, const double* phi, double ms, double sig
 hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma, const void* b, void* x,
                          double tol, double a, int maxit, hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_solve_fcg");
   const double t0 = now_s();
   HMC_TRY(solve_checks(c, ms, sigma, b, x, 64, tol, maxit));
   if (!(a > 0.0)) return fail(c, HMC_ERR_INVALID, "a must be positive");
@@ -557,6 +565,21 @@ hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   c->tuned32 = false;
   c->persist32 = false;
   destroy_graphs(c);
+  return HMC_OK;
+}
+
+hmc_status hmc_set_batched_variant(hmc_ctx* c, int variant) {
+  if (!c) return HMC_ERR_INVALID;
+  if (variant < 0 || variant > 2) return fail(c, HMC_ERR_INVALID, "variant must be 0, 1 or 2");
+  c->batch_variant = variant;
+  c->batch_choice = 0;
+  c->batch_us[0] = c->batch_us[1] = 0.f;
+  return HMC_OK;
+}
+
+hmc_status hmc_batched_variant(hmc_ctx* c, int* variant) {
+  if (!c || !variant) return HMC_ERR_INVALID;
+  *variant = c->batch_variant ? c->batch_variant : c->batch_choice;
   return HMC_OK;
 }
 

@@ -22,6 +22,7 @@
 
 #include "operator.cuh"
 #include "solvers.h"
+#include "trace.h"
 #include "validate.h"
 
 namespace hmc {
@@ -93,10 +94,10 @@ __device__ __forceinline__ double block_total(double v) {
 // Second half of group_sum: thread 0 holds the block total; the last block of
 // the system's group sums the partials (in FP64, that block only).
 __device__ __forceinline__ bool group_finish(double blocktot, double* partials, int base, int count,
-                                             unsigned* ticket, double* tot) {
+                                             unsigned* ticket, double* tot, int vb) {
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = blocktot;
+    partials[vb] = blocktot;
     __threadfence();
     unsigned t = atomicAdd(ticket, 1u);
     am_last = (t == (unsigned)count - 1u);
@@ -128,6 +129,19 @@ struct BScal {
   __syncthreads();                                   \
   const Geo& g = S_.g;                               \
   const int lb = blockIdx.x - S_.block0;             \
+  const int stride = S_.nblocks * blockDim.x
+
+// The same for virtual block vb of a persistent launch, whose blocks take one
+// virtual block after another (the leading barrier keeps the previous one's
+// readers of the shared copy ahead of the new write).
+#define VBLOCK_SYS(vb)                               \
+  __shared__ BSys S_;                                \
+  const int s_ = bsys[vb];                           \
+  __syncthreads();                                   \
+  if (threadIdx.x == 0) S_ = sys[s_];                \
+  __syncthreads();                                   \
+  const Geo& g = S_.g;                               \
+  const int lb = (vb) - S_.block0;                   \
   const int stride = S_.nblocks * blockDim.x
 
 __global__ void kb_phase(const BSys* __restrict__ sys, const int* __restrict__ bsys,
@@ -190,13 +204,13 @@ __global__ void kb_init(const BSys* __restrict__ sys, const int* __restrict__ bs
 // p_new = r + beta p_old (beta = 0 on a system's first iteration), evaluated
 // at every stencil point it reads; u = M^dagger p_new; per-system <p, A p>.
 template <typename R>
-__global__ void __launch_bounds__(512) kb_cg_pmdag(const BSys* __restrict__ sys, const int* __restrict__ bsys,
-                                                   BState* bst, const double2* __restrict__ E,
-                                                   const float* __restrict__ p32, const V2<R>* __restrict__ r,
-                                                   const V2<R>* __restrict__ pold, V2<R>* __restrict__ pnew,
-                                                   V2<R>* __restrict__ u, double* partials, unsigned* tickets,
-                                                   unsigned* ndone) {
-  BLOCK_SYS();
+__device__ __forceinline__ void pmdag_body(int vb, const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                           BState* bst, const double2* __restrict__ E,
+                                           const float* __restrict__ p32, const V2<R>* __restrict__ r,
+                                           const V2<R>* __restrict__ pold, V2<R>* __restrict__ pnew,
+                                           V2<R>* __restrict__ u, double* partials, unsigned* tickets,
+                                           unsigned* ndone) {
+  VBLOCK_SYS(vb);
   __shared__ BScal<R> sc;
   __shared__ int skip;
   if (threadIdx.x == 0) {
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(512) kb_cg_pmdag(const BSys* __restrict__ sys,
   }
   const double bt = block_total(loc);
   double tot;
-  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot) && threadIdx.x == 0) {
+  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot, vb) && threadIdx.x == 0) {
     CGScal& c = bst[s_].cg;
     c.pAp = tot;
     if (!(tot > 0.0) || !isfinite(tot)) {
@@ -249,13 +263,23 @@ __global__ void __launch_bounds__(512) kb_cg_pmdag(const BSys* __restrict__ sys,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, const int* __restrict__ bsys,
-                                               BState* bst, const double2* __restrict__ E,
-                                               const float* __restrict__ p32, const V2<R>* __restrict__ u,
-                                               const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
-                                               V2<R>* __restrict__ r, double* partials, unsigned* tickets,
-                                               unsigned* ndone) {
-  BLOCK_SYS();
+__global__ void __launch_bounds__(512) kb_cg_pmdag(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                   BState* bst, const double2* __restrict__ E,
+                                                   const float* __restrict__ p32, const V2<R>* __restrict__ r,
+                                                   const V2<R>* __restrict__ pold, V2<R>* __restrict__ pnew,
+                                                   V2<R>* __restrict__ u, double* partials, unsigned* tickets,
+                                                   unsigned* ndone) {
+  pmdag_body<R>(blockIdx.x, sys, bsys, bst, E, p32, r, pold, pnew, u, partials, tickets, ndone);
+}
+
+template <typename R>
+__device__ __forceinline__ void m_body(int vb, const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                       BState* bst, const double2* __restrict__ E,
+                                       const float* __restrict__ p32, const V2<R>* __restrict__ u,
+                                       const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
+                                       V2<R>* __restrict__ r, double* partials, unsigned* tickets,
+                                       unsigned* ndone) {
+  VBLOCK_SYS(vb);
   __shared__ BScal<R> sc;
   __shared__ int skip;
   if (threadIdx.x == 0) {
@@ -291,7 +315,7 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
   }
   const double bt = block_total(loc);
   double tot;
-  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot) && threadIdx.x == 0) {
+  if (group_finish(bt, partials, S_.block0, S_.nblocks, tickets + s_, &tot, vb) && threadIdx.x == 0) {
     CGScal& c = bst[s_].cg;
     const double rr = tot;
     c.beta = rr / c.rr;
@@ -304,6 +328,50 @@ __global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, con
     else if (c.iter >= c.maxit)
       c.done = CG_MAXIT;
     if (c.done) atomicAdd(ndone, 1u);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) kb_cg_m(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                               BState* bst, const double2* __restrict__ E,
+                                               const float* __restrict__ p32, const V2<R>* __restrict__ u,
+                                               const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
+                                               V2<R>* __restrict__ r, double* partials, unsigned* tickets,
+                                               unsigned* ndone) {
+  m_body<R>(blockIdx.x, sys, bsys, bst, E, p32, u, p, x, r, partials, tickets, ndone);
+}
+
+// The batched CG as ONE persistent cooperative launch: the grid's blocks take
+// the plan's virtual blocks (one group per system) in turn, and the two halves
+// of an iteration -- the same bodies as kb_cg_pmdag and kb_cg_m -- are
+// separated by grid barriers instead of kernel boundaries. Every 8 iterations
+// the blocks read the count of finished systems between two barriers (no body
+// runs there, so all blocks read the same count) and leave together once every
+// running system is done. Barrier waits are bounded: a wait that gives up sets
+// gb->err and every block leaves.
+template <typename R>
+__global__ void __launch_bounds__(512) kb_cg_persist(const BSys* __restrict__ sys, const int* __restrict__ bsys,
+                                                     int nvb, BState* bst, const double2* __restrict__ E,
+                                                     const float* __restrict__ p32, V2<R>* __restrict__ x,
+                                                     V2<R>* __restrict__ r, V2<R>* __restrict__ p,
+                                                     V2<R>* __restrict__ q, V2<R>* __restrict__ u, double* partials,
+                                                     unsigned* tickets, unsigned* ndone, unsigned target,
+                                                     int max_iters, GridBar* gb, long long limit,
+                                                     unsigned expect) {
+  for (int it = 0; it < max_iters; ++it) {
+    V2<R>* pold = (it & 1) ? q : p;
+    V2<R>* pnew = (it & 1) ? p : q;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
+      pmdag_body<R>(vb, sys, bsys, bst, E, p32, r, pold, pnew, u, partials, tickets, ndone);
+    if (!grid_barrier(gb, expect, limit)) return;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
+      m_body<R>(vb, sys, bsys, bst, E, p32, u, pnew, x, r, partials, tickets, ndone);
+    if (!grid_barrier(gb, expect, limit)) return;
+    if ((it & 7) == 7) {
+      const unsigned d = __ldcg(ndone);
+      if (!grid_barrier(gb, expect, limit)) return;
+      if (d >= target) return;
+    }
   }
 }
 
@@ -543,8 +611,71 @@ static hmc_status autotune(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<
   return HMC_OK;
 }
 
+template <typename R>
+static hmc_status batched_cg_loop(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p, V2<R>* q,
+                                  V2<R>* u, int maxit, int pre_done, int chunk, int kid, double bytes_iter,
+                                  long long* iters_launched);
+
+// Resident blocks of the persistent batched kernel at `threads` per block.
+template <typename R>
+static int persist_capacity(hmc_ctx* c, int threads) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_cg_persist<R>, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ * c->nsm;
+}
+
+// The FP32 CG of all active systems as one persistent cooperative launch (the
+// states left by kb_init; see kb_cg_persist). *ran is false when the launch
+// does not fit (no resident block), and the caller takes the graph loop.
+template <typename R>
+static hmc_status batched_cg_persist(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p,
+                                     V2<R>* q, V2<R>* u, int maxit, int pre_done, bool* ran) {
+  *ran = false;
+  const int cap = persist_capacity<R>(c, w.threads);
+  if (cap < 1) return HMC_OK;
+  int grid = std::min(w.blocks, cap);
+  HMC_CUDA(c, cudaMemsetAsync(c->gbar, 0, sizeof(GridBar), s));
+  const BSys* sys = w.sys;
+  const int* bsys = w.bsys;
+  int nvb = w.blocks;
+  BState* bst = w.st;
+  const double2* E = w.E;
+  const float* p32 = w.phi32;
+  double* partials = w.partials;
+  unsigned* tickets = w.tickets;
+  unsigned* ndone = w.ndone;
+  unsigned target = (unsigned)(w.nsys - pre_done);
+  int max_iters = maxit + 1;
+  GridBar* gb = c->gbar;
+  long long limit = c->bar_limit > 0 ? c->bar_limit : 2000000000LL;  // about one second of SM clock
+  unsigned expect = (unsigned)grid + (unsigned)c->bar_extra;
+  void* args[] = {&sys, &bsys, &nvb, &bst, &E, &p32, &x, &r, &p, &q, &u, &partials, &tickets, &ndone,
+                  &target, &max_iters, &gb, &limit, &expect};
+  const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
+  cudaEvent_t a = nullptr;
+  prof_begin(c, kid, &a);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)kb_cg_persist<R>, dim3(grid), dim3(w.threads),
+                                                    args, 0, s);
+  prof_end(c, kid, a);
+  if (e != cudaSuccess) return cuda_fail(c, e, "persistent batched CG launch");
+  GridBar gh{};
+  HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s));
+  HMC_CUDA(c, cudaMemcpyAsync(&gh, c->gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+  HMC_CUDA(c, cudaStreamSynchronize(s));
+  if (gh.err) return fail(c, HMC_ERR_TIMEOUT, "persistent batched CG: a grid barrier wait gave up");
+  double bytes = 0.0;
+  for (int i = 0; i < w.nsys; ++i) bytes += (double)w.st_host[i].cg.iter * w.hsys[i].g.N * (sizeof(R) == 8 ? 192.0 : 88.0);
+  c->prof.bytes[kid] += bytes;
+  *ran = true;
+  return HMC_OK;
+}
+
 // Run CG on all active systems in precision R until every system is done,
-// replaying a captured graph of `chunk` iterations.
+// replaying a captured graph of `chunk` iterations, or (FP32, when chosen) as
+// one persistent launch.
 template <typename R>
 static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>* b, V2<R>* x, V2<R>* r,
                              V2<R>* p, V2<R>* q, V2<R>* u, int maxit, int nactive, long long* iters_launched) {
@@ -563,6 +694,54 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   const int chunk = 8;
   const int kid = sizeof(R) == 8 ? K_BATCH_CG64 : K_BATCH_CG32;
   const double bytes_iter = sizeof(R) == 8 ? 192.0 : 88.0;
+  // FP32: the persistent launch when pinned, or by timing -- the first solve of
+  // the context takes the graph loop, the second the persistent launch, and
+  // the one with the shorter time per iteration is kept
+  if constexpr (sizeof(R) == 4) {
+    int v = c->batch_variant ? c->batch_variant : c->batch_choice;
+    const bool probe = (c->batch_variant == 0 && c->batch_choice == 0);
+    if (probe) v = (c->batch_us[0] > 0.f) ? 2 : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (probe) {
+      HMC_CUDA(c, cudaEventCreate(&e0));
+      HMC_CUDA(c, cudaEventCreate(&e1));
+      HMC_CUDA(c, cudaEventRecord(e0, s));
+    }
+    bool done = false;
+    if (v == 2) {
+      HMC_TRY(batched_cg_persist<R>(c, w, s, x, r, p, q, u, maxit, pre_done, &done));
+      if (!done) v = 1;
+    }
+    if (!done) {
+      HMC_TRY(batched_cg_loop<R>(c, w, s, x, r, p, q, u, maxit, pre_done, chunk, kid, bytes_iter,
+                                 iters_launched));
+    }
+    if (probe) {
+      HMC_CUDA(c, cudaEventRecord(e1, s));
+      HMC_CUDA(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      HMC_CUDA(c, cudaMemcpyAsync(w.st_host, w.st, sizeof(BState) * w.nsys, cudaMemcpyDeviceToHost, s));
+      HMC_CUDA(c, cudaStreamSynchronize(s));
+      int iters = 1;
+      for (int i = 0; i < w.nsys; ++i) iters = std::max(iters, w.st_host[i].cg.iter);
+      c->batch_us[v == 2 ? 1 : 0] = 1e3f * ms / iters;
+      if (c->batch_us[0] > 0.f && c->batch_us[1] > 0.f) c->batch_choice = c->batch_us[1] < c->batch_us[0] ? 2 : 1;
+      if (v == 1 && c->batch_us[0] > 0.f && persist_capacity<R>(c, w.threads) < 1) c->batch_choice = 1;
+    }
+    (void)nactive;
+    return HMC_OK;
+  }
+  return batched_cg_loop<R>(c, w, s, x, r, p, q, u, maxit, pre_done, chunk, kid, bytes_iter, iters_launched);
+}
+
+// The graph-loop form of batched_cg after kb_init.
+template <typename R>
+static hmc_status batched_cg_loop(hmc_ctx* c, BatchWs& w, cudaStream_t s, V2<R>* x, V2<R>* r, V2<R>* p, V2<R>* q,
+                                  V2<R>* u, int maxit, int pre_done, int chunk, int kid, double bytes_iter,
+                                  long long* iters_launched) {
   // One graph launch for the whole batched solve: a device-side while loop
   // repeats the captured chunk until every running system is done (counted
   // in ndone) or the trip bound maxit / chunk + 2 is reached.
@@ -593,7 +772,6 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
       c->prof.bytes[kid] += bytes;
       c->prof.launches[kid] += 2 * launched;
       *iters_launched += launched;
-      (void)nactive;
       return HMC_OK;
     }
     c->err.clear();  // fall back to the chunked loop below
@@ -648,7 +826,6 @@ static hmc_status batched_cg(hmc_ctx* c, BatchWs& w, cudaStream_t s, const V2<R>
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
   *iters_launched += launched;
-  (void)nactive;
   return status;
 }
 
@@ -659,6 +836,7 @@ using namespace hmc;
 extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* sys, int mixed,
                                         hmc_solve_info* infos) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_solve_batched");
   if (nsys < 1 || !sys) return fail(c, HMC_ERR_INVALID, "nsys must be >= 1 and sys non-NULL");
   if (mixed != 0 && mixed != 1) return fail(c, HMC_ERR_INVALID, "mixed must be 0 or 1");
   BatchWs w;

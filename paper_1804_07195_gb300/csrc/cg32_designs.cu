@@ -475,43 +475,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m_march(Geo g, Phase<float
 // replaced by grid barriers and the block partials summed by every block in
 // the same fixed order. The barrier waits are bounded: a wait that gives up
 // marks the solve CG_TIMEOUT and every block leaves.
-__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long long limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &gb->gen;
-    volatile int* verr = &gb->err;
-    int ok = (*verr == 0);
-    if (ok) {
-      const unsigned my = *vgen;
-      __threadfence();
-      if (atomicAdd(&gb->count, 1u) == nblocks - 1u) {
-        atomicExch(&gb->count, 0u);
-        __threadfence();
-        atomicAdd(&gb->gen, 1u);
-      } else {
-        const long long t0 = clock64();
-        while (*vgen == my) {
-          if (*verr) {
-            ok = 0;
-            break;
-          }
-          if (clock64() - t0 > limit) {
-            atomicExch(&gb->err, 1);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      __threadfence();
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 constexpr int kPersistThreads = 256;
 
 __global__ void __launch_bounds__(kPersistThreads, 4)

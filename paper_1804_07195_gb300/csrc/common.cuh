@@ -252,6 +252,47 @@ struct GridBar {
   int pad;
 };
 
+// Barrier over all blocks of a cooperative launch. The wait of each block is
+// bounded by `limit` SM clock cycles: a block that gives up sets gb->err, and
+// every later barrier returns false at once, so the kernel can leave cleanly
+// (the host reports a timeout). Returns true when the barrier was passed.
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    volatile int* verr = &gb->err;
+    int ok = (*verr == 0);
+    if (ok) {
+      const unsigned my = *vgen;
+      __threadfence();
+      if (atomicAdd(&gb->count, 1u) == nblocks - 1u) {
+        atomicExch(&gb->count, 0u);
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*vgen == my) {
+          if (*verr) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > limit) {
+            atomicExch(&gb->err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Float-float sums for the FP32 kernels. GB300 executes FP64 at 1/58 of the FP32
 // rate, so the single-precision kernels keep their reductions off the FP64

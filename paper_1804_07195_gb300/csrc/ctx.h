@@ -164,6 +164,11 @@ struct hmc_ctx {
   int bar_extra = 0;         // test hook: extra arrivals every grid barrier waits for
   long long bar_limit = 0;   // test hook: barrier wait limit in SM cycles (0: default)
 
+  // batched FP32 CG: 0 = choose by timing, 1 = graph loop of per-iteration
+  // kernels, 2 = one persistent cooperative launch per solve
+  int batch_variant = 0;
+  int batch_choice = 0;                // the variant chosen (0: not yet)
+  float batch_us[2] = {0.f, 0.f};      // us per iteration measured for 1 and 2
   // per-chain contexts of hmc_md_trajectory_batched (slot i: chain i of the
   // last call; recreated when a chain's lattice changes), destroyed with ctx
   std::vector<hmc_ctx*> subs;

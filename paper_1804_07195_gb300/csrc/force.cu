@@ -6,6 +6,7 @@
 #include <string>
 
 #include "force.h"
+#include "trace.h"
 
 namespace hmc {
 
@@ -47,6 +48,7 @@ static hmc_status term_solve(hmc_ctx* c, int nmass, const double* masses, const 
 
 hmc_status term_grad(hmc_ctx* c, int nmass, const double* masses, const double2* const* chi, int i,
                      const hmc_solver_opts* o, double* grad, SolveStats* st) {
+  HMC_TRACE("force term");
   const Geo& g = c->geo;
   const double2* src;
   double2* eta;
@@ -147,6 +149,7 @@ hmc_status hmc_make_chi(hmc_ctx* c, const double* phi, int nmass, const double* 
                         const void* const* rho, void* const* chi, const hmc_solver_opts* opts,
                         hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_make_chi");
   HMC_TRY(check_masses(c, nmass, masses));
   HMC_TRY(check_chi(c, nmass, rho, "rho"));
   HMC_TRY(check_chi(c, nmass, (const void* const*)chi, "chi"));
@@ -163,6 +166,7 @@ hmc_status hmc_force(hmc_ctx* c, const double* phi, int nmass, const double* mas
                      const void* const* chi, int term, int flags, const hmc_solver_opts* opts,
                      double* dSdphi, hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_force");
   if (!dSdphi || ((uintptr_t)dSdphi) % 8) return fail(c, HMC_ERR_INVALID, "dSdphi NULL or misaligned");
   HMC_TRY(check_masses(c, nmass, masses));
   if (term < -1 || term > nmass) return fail(c, HMC_ERR_INVALID, "term out of range");
@@ -198,6 +202,7 @@ hmc_status hmc_action(hmc_ctx* c, const double* phi, int nmass, const double* ma
                       const void* const* chi, int term, int flags, const hmc_solver_opts* opts,
                       double* S_out, hmc_solve_info* info) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_action");
   if (!S_out) return fail(c, HMC_ERR_INVALID, "S_out is NULL");
   HMC_TRY(check_masses(c, nmass, masses));
   if (term < -1 || term > nmass) return fail(c, HMC_ERR_INVALID, "term out of range");

@@ -632,11 +632,12 @@ static hmc_status tune_fused(hmc_ctx* c, const Geo& g, R dm, R sigma, const V2<R
   std::vector<FusedShape> cands;
   const bool aligned16 = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
   for (int pairs : {1, 0})
-    for (int TX : {32, 64})
+    for (int TX : {16, 32, 64})
       for (int Tj : {4, 6, 8, 14, 30})
         for (int Tt : {4, 8, 16, 64})
           for (int D : {2, 6}) {
             if (pairs && !aligned16) continue;
+            if (!pairs && TX == 16) continue;
             // pairs: TX threads per box row carry 2 TX cells, Ti = 2 (TX - 2)
             FusedShape fs = make_fused_shape(g, pairs ? 2 * (TX - 2) : TX - 2, Tj, Tt, D, pairs);
             if (pairs && (fs.Ti & 1)) continue;
@@ -656,7 +657,7 @@ static hmc_status tune_fused(hmc_ctx* c, const Geo& g, R dm, R sigma, const V2<R
   for (const FusedShape& fs : cands) {
     fused_raw_launch<R>(c, g, fs, dm, sigma, in, out);  // warm
     HMC_CUDA(c, cudaEventRecord(e0, c->stream));
-    for (int rep = 0; rep < 3; ++rep) fused_raw_launch<R>(c, g, fs, dm, sigma, in, out);
+    for (int rep = 0; rep < 5; ++rep) fused_raw_launch<R>(c, g, fs, dm, sigma, in, out);
     HMC_CUDA(c, cudaEventRecord(e1, c->stream));
     HMC_CUDA(c, cudaEventSynchronize(e1));
     HMC_CUDA(c, cudaGetLastError());

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "hmc.h"
+#include "trace.h"
 
 namespace hmc {
 
@@ -72,10 +73,14 @@ void run_integrator(MDT& md, int kind, const std::vector<int>& steps, int nmd, d
     nest.ratio.push_back(steps[0]);
     for (size_t k = 1; k < steps.size(); ++k) nest.ratio.push_back(steps[k] / steps[k - 1]);
     const double h0s = tau / steps[0];
-    for (int i = 0; i < steps[0] && md.ok(); ++i) nest.step(0, h0s);
+    for (int i = 0; i < steps[0] && md.ok(); ++i) {
+      HMC_TRACE("md step");
+      nest.step(0, h0s);
+    }
   } else if (kind == HMC_INTEG_LEAPFROG) {
     const double h = tau / nmd;
     for (int i = 0; i < nmd && md.ok(); ++i) {
+      HMC_TRACE("md step");
       md.Q(0.5 * h);
       md.P(-1, h);
       md.Q(0.5 * h);
@@ -83,6 +88,7 @@ void run_integrator(MDT& md, int kind, const std::vector<int>& steps, int nmd, d
   } else {
     const double h = tau / nmd;
     for (int i = 0; i < nmd && md.ok(); ++i) {
+      HMC_TRACE("md step");
       md.P(-1, h / 6.0);
       md.Q(0.5 * h);
       md.fg_kick((2.0 / 3.0) * h, h);

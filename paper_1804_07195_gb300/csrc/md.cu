@@ -14,6 +14,7 @@
 
 #include "force.h"
 #include "integrator.h"
+#include "trace.h"
 
 namespace hmc {
 
@@ -45,6 +46,7 @@ struct MD {
 
   // dS_k/dphi at the current phi into `out` (level -1: all levels summed).
   hmc_status level_grad(int k, double* out) {
+    HMC_TRACE("force level");
     HMC_TRY(tables());
     ++nforce;
     if (k == -1) {
@@ -123,6 +125,7 @@ extern "C" hmc_status hmc_md_trajectory(hmc_ctx* c, double* phi, double* pi, int
                                         const hmc_solver_opts* action_opts, double* H0, double* H1,
                                         hmc_solve_info* agg) {
   if (!c) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_md_trajectory");
   if (!phi || !pi || !integ || !md_opts || !action_opts || !H0 || !H1 || !rho)
     return fail(c, HMC_ERR_INVALID, "NULL argument");
   if (((uintptr_t)phi) % 8 || ((uintptr_t)pi) % 8) return fail(c, HMC_ERR_INVALID, "phi/pi misaligned");

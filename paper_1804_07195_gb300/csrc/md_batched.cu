@@ -18,6 +18,7 @@
 
 #include "force.h"
 #include "integrator.h"
+#include "trace.h"
 #include "validate.h"
 
 namespace hmc {
@@ -114,6 +115,7 @@ struct BatchMD {
 
   // dS_k/dphi of every chain into its cache slot (level -1: all levels).
   hmc_status level_grad(int k, int slot) {
+    HMC_TRACE("force level, all chains");
     HMC_TRY(tables());
     for (BChain& b : ch) {
       double* out = b.cache + (size_t)slot * b.N();
@@ -215,6 +217,7 @@ extern "C" hmc_status hmc_md_trajectory_batched(hmc_ctx* ctx, int nchains, const
                                                 const hmc_solver_opts* md_opts, const hmc_solver_opts* action_opts,
                                                 double* H0, double* H1, hmc_solve_info* infos) {
   if (!ctx) return HMC_ERR_INVALID;
+  HMC_TRACE("hmc_md_trajectory_batched");
   ctx->err.clear();
   const hmc_status s =
       trajectory_batched(ctx, nchains, chains, nmass, masses, integ, md_opts, action_opts, H0, H1, infos);

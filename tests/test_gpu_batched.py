@@ -36,6 +36,61 @@ def check(instances, xs, infos, tol):
         assert abs(info["true_rel_res"] - rel) <= 1e-3 * tol + 1e-14
 
 
+def run_batch_variant(instances, mixed, variant, tol=1e-10):
+    import paper_1804_07195_gb300 as hmc
+    systems = []
+    for w, ms, sigma, b in instances:
+        p = w.lat
+        systems.append({"lattice": hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta), "phi": dev(w.phi),
+                        "ms": ms, "sigma": sigma, "b": dev(b), "x": torch.zeros(p.nsites, dtype=torch.complex128, device="cuda"),
+                        "tol": tol, "maxit": 100000})
+    with ctx_for(instances[0][0].lat) as ctx:
+        ctx.set_batched_variant(variant)
+        infos = ctx.solve_batched(systems, mixed=mixed)
+        used = ctx.batched_variant()
+    return [host(s["x"]) for s in systems], infos, used
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_fp32_batched_designs(variant):
+    """The two designs of the batched FP32 CG (graph loop of per-iteration
+    kernels; one persistent cooperative launch with grid barriers) under FP64
+    defect correction: every system's true residual against the oracle."""
+    need_gpu()
+    shapes = [(1, 1, 2), (3, 3, 8), (6, 6, 16), (2, 5, 4), (12, 12, 16), (4, 3, 10), (18, 18, 32)]
+    inst = []
+    for k, sh in enumerate(shapes):
+        w = W.small(*sh, seed=320 + k, U=3.0, beta=6.0)
+        inst.append((w, [0.0, 0.1, 0.5, 2.0][k % 4], [0.0, 0.0, 0.04][k % 3], w.b))
+    xs, infos, used = run_batch_variant(inst, 1, variant)
+    assert used == variant
+    check(inst, xs, infos, 1e-10)
+
+
+def test_persistent_batched_wait_times_out_and_context_survives():
+    """The persistent batched kernel's grid barriers wait a bounded number of
+    SM cycles: with the test hook making every barrier wait for one arrival
+    that never comes, the solve returns HMC_ERR_TIMEOUT, and after the hook is
+    cleared the same context solves correctly."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.small(6, 6, 16, seed=330, U=3.0, beta=6.0)
+    p = w.lat
+    lat = hmc.Lattice(p.n, p.m, p.nt, p.kappa, p.U, p.beta)
+    mk = lambda: [{"lattice": lat, "phi": dev(w.phi), "ms": 0.1, "b": dev(w.b),
+                   "x": torch.zeros(p.nsites, dtype=torch.complex128, device="cuda")}]
+    with ctx_for(p) as ctx:
+        ctx.set_batched_variant(2)
+        ctx.set_wait_test(1, 2_000_000)
+        with pytest.raises(hmc.HMCError) as e:
+            ctx.solve_batched(mk(), mixed=True)
+        assert e.value.status == -5
+        ctx.set_wait_test(0, 0)
+        sy = mk()
+        infos = ctx.solve_batched(sy, mixed=True)
+    check([(w, 0.1, 0.0, w.b)], [host(sy[0]["x"])], infos, 1e-10)
+
+
 @pytest.mark.parametrize("mixed", [0, 1])
 def test_uneven_small_batch(mixed):
     need_gpu()

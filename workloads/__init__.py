@@ -138,6 +138,27 @@ def batch_instances(count: int = 48) -> List[Workload]:
     return out
 
 
+# the batched instances advanced as Markov chains: nested Omelyan, N_MD and
+# time-scale ratios for the three masses
+BATCH_NMD = 8
+BATCH_NI = (2, 1, 1)
+
+
+def batch_chains(instances: List[Workload]) -> List[tuple]:
+    """Momenta and heat-bath vectors for running the batched instances as
+    Markov chains: per instance (its lattice and phi), pi ~ N(0,1) and one
+    complex Gaussian rho per Hasenbusch term (masses + 1), drawn from a stream
+    of their own. Returns [(pi, [rho_0, ..., rho_n]), ...]."""
+    out = []
+    children = np.random.SeedSequence(SEEDS["batch48"] + 100).spawn(len(instances))
+    for w, child in zip(instances, children):
+        g = rng(child)
+        pi = draw_pi(g, w.lat.nsites)
+        rho = [draw_complex(g, w.lat.nsites) for _ in range(len(w.masses) + 1)]
+        out.append((pi, rho))
+    return out
+
+
 def small(n, m, nt, seed, kappa=1.0, U=2.0, beta=4.0, masses=()) -> Workload:
     """A small lattice for tests (ragged sizes, n or m down to 1)."""
     lat = LatticeParams(n, m, nt, kappa, U, beta)

@@ -248,13 +248,13 @@ def main():
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs",
                              "mmdag32_stream", "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64",
-                             "batched", "force", "md_short"],
+                             "batched", "force", "md_short", "trajectory"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.kernel_case:
-        kernel_case(args.kernel_case, args.graph_mode)
+        kernel_case(args.kernel_case, args.graph_mode, args.cg_variant, args.fgmres_a)
         return
 
     if args.impl == "reference":
@@ -786,9 +786,10 @@ def aggregate_over_ranks(ms, work, dist, device=None):
     return float(t.item()), float(w.item())
 
 
-def kernel_case(case, graph_mode=2):
-    """One solve (or 20 operator applications) on the 102x102x64 lattice: the
-    case the ncu kernel profiles are taken on."""
+def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
+    """One solve (or 20 operator applications, a force, a trajectory) on the
+    102x102x64 lattice: the cases the ncu kernel profiles and launch lists are
+    taken on."""
     import torch
     import paper_1804_07195_gb300 as hmc
     from paper_1804_07195_gb300 import build
@@ -852,6 +853,19 @@ def kernel_case(case, graph_mode=2):
             opts = hmc.SolverOpts(method=1, tol=1e-10, a=1.0)
             chis, _ = ctx.make_chi(phi, masses, rho, opts=opts)
             _, info = ctx.force(phi, masses, chis, opts=opts)
+        elif case == "trajectory":
+            # two trajectories of the benchmark step (the first one warms the
+            # tuners and graphs); launch lists skip the first
+            if cg_variant:
+                ctx.set_cg_variant(cg_variant)
+            masses = list(W.L102_MASSES)
+            rho = [torch.tensor(r, device="cuda") for r in w.rho]
+            integ = hmc.Integrator(0, W.L102_NMD, W.L102_NI, W.OMELYAN_ZETA, 1.0)
+            md = hmc.SolverOpts(method=1, tol=1e-10, a=fgmres_a)
+            act = hmc.SolverOpts(method=1, tol=1e-12, a=fgmres_a)
+            for _ in range(2):
+                H0, H1, info = ctx.md_trajectory(phi.clone(), torch.tensor(w.pi, device="cuda"), masses, rho, integ,
+                                                 md, act)
         elif case == "md_short":
             # a short trajectory of the benchmark's kind (N_MD = 6, time scales 2, 1, 1):
             # the MD updates, energies and forces of the path

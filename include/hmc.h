@@ -347,7 +347,7 @@ hmc_status hmc_set_apply_variant(hmc_ctx* ctx, int variant);
 hmc_status hmc_apply_variant(hmc_ctx* ctx, int prec, int* variant);
 /* Pin the fused kernel's tile for precision prec: Ti x Tj cells per block
  * (clamped to the lattice), Tt time slices per block, `depth` time slices
- * staged ahead of the one in use (2 or 6), and pairs = 1 for the FP32 kernel
+ * staged ahead of the one in use (2 or 6 in FP32, 2 in FP64), and pairs = 1 for the FP32 kernel
  * whose threads own two neighbouring cells as one 16-byte complex64 pair
  * (n and Ti even; (Ti/2+2)(Tj+2) <= 256 threads) or 0 for one cell per thread
  * ((Ti+2)(Tj+2) <= 1024 threads in FP32, 512 in FP64). Without it the tile

@@ -567,6 +567,7 @@ template <typename R>
 bool fused_ok(const Geo& g, const FusedShape& fs) {
   const int NT = fused_threads_of<R>(fs);
   if (!fused_depth_ok(fs.D)) return false;
+  if (sizeof(R) == 8 && fs.D != 2) return false;  // FP64: depth 2 only (the deeper ring spills registers)
   if (fs.pairs) {
     // FP32 only; pairs of cells stay aligned in memory and inside the box
     if (sizeof(R) != 4 || (g.n & 1) || (fs.Ti & 1) || fs.Ti < 2 || NT > kPairMaxThreads) return false;
@@ -586,7 +587,8 @@ static void fused_raw_launch(hmc_ctx* c, const Geo& g, const FusedShape& fs, R d
   const unsigned long long bit = 1ull << (c->device & 63);
   if (!(attr_set & bit)) {
     cudaFuncSetAttribute(k_mmdag_fused<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_mmdag_fused<R, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if constexpr (sizeof(R) == 4)
+      cudaFuncSetAttribute(k_mmdag_fused<R, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set |= bit;
   }
   const int NT = fused_threads_of<R>(fs);
@@ -615,9 +617,12 @@ static void fused_raw_launch(hmc_ctx* c, const Geo& g, const FusedShape& fs, R d
     ph = (const float*)c->ws[WS_PHI32];
   else
     ph = (const double2*)c->ws[WS_E];
-  switch (fs.D) {
-    case 2: k_mmdag_fused<R, 2><<<blocks, threads, smem, c->stream>>>(g, fs, ph, dm, sigma, in, out); break;
-    default: k_mmdag_fused<R, 6><<<blocks, threads, smem, c->stream>>>(g, fs, ph, dm, sigma, in, out); break;
+  if constexpr (sizeof(R) == 8) {
+    k_mmdag_fused<R, 2><<<blocks, threads, smem, c->stream>>>(g, fs, ph, dm, sigma, in, out);
+  } else if (fs.D == 2) {
+    k_mmdag_fused<R, 2><<<blocks, threads, smem, c->stream>>>(g, fs, ph, dm, sigma, in, out);
+  } else {
+    k_mmdag_fused<R, 6><<<blocks, threads, smem, c->stream>>>(g, fs, ph, dm, sigma, in, out);
   }
 }
 

@@ -20,6 +20,8 @@ SHAPES = [(1, 1, 2), (2, 1, 4), (1, 3, 5), (3, 3, 8), (2, 5, 3), (6, 6, 16), (7,
           (36, 36, 64)]
 # (Ti, Tj, Tt, depth): default-like, ragged in every direction, the smallest tile, each depth
 TILES = [(30, 8, 16, 2), (5, 3, 7, 2), (1, 1, 1, 6), (62, 6, 64, 2), (30, 6, 5, 6), (4, 4, 2, 2)]
+# FP64 takes depth 2 only
+TILES64 = [t for t in TILES if t[3] == 2]
 
 
 def fused_ctx(w, prec, tile=None):
@@ -37,7 +39,7 @@ def test_fused_fp64_matches_oracle(shape, ms, sigma):
     w = W.small(*shape, seed=1200 + sum(shape))
     ol = OLat.from_params(w.lat)
     ref = of.apply_MMdag(ol, w.phi, ms, w.b, sigma)
-    for tile in [None] + [t + (0,) for t in TILES]:
+    for tile in [None] + [t + (0,) for t in TILES64]:
         with fused_ctx(w, 64, tile) as ctx:
             got = host(ctx.apply_MMdag(dev(w.phi), ms, dev(w.b), sigma))
             assert ctx.apply_variant(64) == 2
@@ -139,4 +141,6 @@ def test_fused_tile_limits():
             ctx.set_fused_tile(32, 62, 30, 8)   # 64 x 32 threads > 1024
         with pytest.raises(hmc.HMCError):
             ctx.set_fused_tile(64, 0, 8, 8)
+        with pytest.raises(hmc.HMCError):
+            ctx.set_fused_tile(64, 30, 8, 8, 6)  # FP64: depth 2 only
         ctx.set_fused_tile(32, 30, 30, 16)      # 32 x 32 = 1024 threads: fits

@@ -462,8 +462,18 @@ def main():
     pi_s, rho_s = dev_inputs[args.warmup]
     phi_f = phi0.clone()
     H0f, H1f, info_f = ctx.md_trajectory(phi_f, pi_s.clone(), masses, rho_s, integ, fp64_md, fp64_act)
+    # the error of the final action at the bench's action tolerance: the same
+    # action (pseudofermions of this step, field phi_f) from mixed solves at 1e-12
+    # and from FP64 CG solves at 1e-14
+    chis_f, _ = ctx.make_chi(phi0, masses, rho_s, opts=hmc.SolverOpts(method=0, tol=1e-14))
+    S12, _ = ctx.action(phi_f, masses, chis_f, opts=act_opts)
+    S14, _ = ctx.action(phi_f, masses, chis_f, opts=hmc.SolverOpts(method=0, tol=1e-14))
     dH_check = {"dH_mixed": float(dH[0]), "dH_fp64": H1f - H0f, "abs_difference": abs(H1f - H0f - dH[0]),
                 "action_true_rel_res_fp64": info_f["true_rel_res"],
+                "action_error_at_1e-12": {"S_mixed_1e-12": S12, "S_fp64_1e-14": S14, "abs_difference": abs(S12 - S14),
+                                          "note": "the action at the end of this trajectory from the bench's "
+                                                  "action solves (mixed, 1e-12) against FP64 CG at 1e-14: what "
+                                                  "the action tolerance contributes to dH"},
                 "settings": "both runs: forces from solves at 1e-10, actions at 1e-12 (mixed: FGMRES with FP32 CG "
                             "inner solves; FP64: CG); the same phi, pi and rho",
                 "note": "the difference is set by the solver tolerance of the MD forces (different rounding of "

@@ -399,6 +399,16 @@ typedef struct {
                            per thread */
 } hmc_kernel_stat;
 
+/* Every device buffer a context allocates carries guard bands of 256 bytes
+ * before and after it, filled with the byte 0xA5. Check them all (synchronises
+ * the context's stream); *nbad receives the number of buffers with a changed
+ * band, and hmc_last_error names the first. A kernel that writes past either
+ * end of a workspace buffer shows up here. */
+hmc_status hmc_check_guards(hmc_ctx* ctx, int* nbad);
+/* Test hook for hmc_check_guards: writes one byte into the band just after the
+ * context's phase table (inside its allocation, no kernel involved). */
+hmc_status hmc_guard_test_write(hmc_ctx* ctx);
+
 /* Per-kernel launch counters are always kept. With timing on, every launch of
  * a library kernel is bracketed by CUDA events on the context's stream and
  * the elapsed times are summed at read time (which synchronises). */

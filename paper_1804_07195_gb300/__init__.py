@@ -371,6 +371,13 @@ class Context:
         `limit_cycles` SM cycles (0: default); (0, 0) restores normal work."""
         self._check(self.lib.hmc_set_wait_test(self.h, extra, limit_cycles))
 
+    def check_guards(self) -> int:
+        """Number of the context's device buffers whose guard bands were
+        overwritten (0 when every kernel stayed inside its buffers)."""
+        n = C.c_int()
+        self._check(self.lib.hmc_check_guards(self.h, C.byref(n)))
+        return n.value
+
     # --- instrumentation ----------------------------------------------------
     def profile(self, timing: bool, reset: bool = True):
         self._check(self.lib.hmc_profile(self.h, 1 if timing else 0, 1 if reset else 0))

@@ -119,6 +119,8 @@ PROTOTYPES = {
     "hmc_set_wait_test": (S, [P, I, C.c_longlong]),
     "hmc_graph_mode": (S, [P, C.POINTER(I)]),
     "hmc_set_graph_mode": (S, [P, I]),
+    "hmc_check_guards": (S, [P, C.POINTER(I)]),
+    "hmc_guard_test_write": (S, [P]),
     "hmc_profile": (S, [P, I, I]),
     "hmc_apply_MMdag_noalloc": (S, [C.POINTER(hmc_lattice), P, D, D, P, P, P]),
     "hmc_profile_read": (S, [P, C.POINTER(hmc_kernel_stat), I, C.POINTER(I)]),

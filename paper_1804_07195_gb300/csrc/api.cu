@@ -26,21 +26,40 @@ hmc_status cuda_fail(hmc_ctx* c, cudaError_t e, const char* what) {
   return HMC_ERR_CUDA;
 }
 
+hmc_status guarded_alloc(hmc_ctx* c, size_t bytes, void** user) {
+  *user = nullptr;
+  unsigned char* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, bytes + 2 * kGuardBytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HMC_ERR_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  // cudaMalloc returns 256-byte aligned memory, so the caller's part keeps that alignment
+  e = cudaMemset(base, kGuardByte, kGuardBytes);
+  if (e == cudaSuccess) e = cudaMemset(base + kGuardBytes + bytes, kGuardByte, kGuardBytes);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    return cuda_fail(c, e, "guard bands");
+  }
+  *user = base + kGuardBytes;
+  return HMC_OK;
+}
+
+void guarded_free(void* user) {
+  if (user) cudaFree((unsigned char*)user - kGuardBytes);
+}
+
 hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out) {
   if (c->ws_bytes[slot] < bytes) {
     if (c->ws[slot]) {
       cudaStreamSynchronize(c->stream);
       destroy_graphs(c);
-      cudaFree(c->ws[slot]);
+      guarded_free(c->ws[slot]);
       c->ws[slot] = nullptr;
       c->ws_bytes[slot] = 0;
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, HMC_ERR_NOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
-    }
+    HMC_TRY(guarded_alloc(c, bytes, &p));
     c->ws[slot] = p;
     c->ws_bytes[slot] = bytes;
   }
@@ -343,9 +362,9 @@ hmc_status hmc_create(hmc_ctx** out, const hmc_lattice* lat, void* stream) {
   c->max_grid = c->nsm * kMaxGridPerSM;
   for (int k = 0; k < K_COUNT; ++k) c->shape[k] = Shape{};
   const size_t N = (size_t)c->geo.N;
-  if ((e = cudaMalloc(&c->ws[WS_E], N * sizeof(double2))) != cudaSuccess) return bail(e);
+  if (guarded_alloc(c, N * sizeof(double2), &c->ws[WS_E]) != HMC_OK) return bail(cudaErrorMemoryAllocation);
   c->ws_bytes[WS_E] = N * sizeof(double2);
-  if ((e = cudaMalloc(&c->ws[WS_PHI32], N * sizeof(float))) != cudaSuccess) return bail(e);
+  if (guarded_alloc(c, N * sizeof(float), &c->ws[WS_PHI32]) != HMC_OK) return bail(cudaErrorMemoryAllocation);
   c->ws_bytes[WS_PHI32] = N * sizeof(float);
   const size_t npart = (size_t)kMaxRed * std::max(c->max_grid, c->nsm * kOneItemBlocksPerSM);
   if ((e = cudaMalloc(&c->partials, sizeof(double) * npart)) != cudaSuccess) return bail(e);
@@ -379,7 +398,7 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   destroy_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int i = 0; i < WS_COUNT; ++i)
-    if (c->ws[i]) cudaFree(c->ws[i]);
+    if (c->ws[i]) guarded_free(c->ws[i]);
   if (c->partials) cudaFree(c->partials);
   if (c->partA) cudaFree(c->partA);
   if (c->partB) cudaFree(c->partB);
@@ -389,7 +408,7 @@ hmc_status hmc_destroy(hmc_ctx* c) {
   if (c->loop_trips) cudaFree(c->loop_trips);
   if (c->loop_trips_host) cudaFreeHost(c->loop_trips_host);
   for (int i = 0; i < hmc_ctx::kBatchSlots; ++i)
-    if (c->bpool[i]) cudaFree(c->bpool[i]);
+    if (c->bpool[i]) guarded_free(c->bpool[i]);
   for (int i = 0; i < 4; ++i)
     if (c->bpool_host[i]) cudaFreeHost(c->bpool_host[i]);
   if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -636,6 +655,40 @@ hmc_status hmc_set_wait_test(hmc_ctx* c, int extra, long long limit_cycles) {
   if (extra < 0 || limit_cycles < 0) return fail(c, HMC_ERR_INVALID, "extra and limit_cycles must be >= 0");
   c->bar_extra = extra;
   c->bar_limit = limit_cycles;
+  return HMC_OK;
+}
+
+hmc_status hmc_check_guards(hmc_ctx* c, int* nbad) {
+  if (!c || !nbad) return HMC_ERR_INVALID;
+  *nbad = 0;
+  HMC_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::string first;
+  unsigned char band[2][kGuardBytes];
+  auto check = [&](void* user, size_t bytes, const std::string& what) -> hmc_status {
+    if (!user) return HMC_OK;
+    const unsigned char* u = (const unsigned char*)user;
+    HMC_CUDA(c, cudaMemcpy(band[0], u - kGuardBytes, kGuardBytes, cudaMemcpyDeviceToHost));
+    HMC_CUDA(c, cudaMemcpy(band[1], u + bytes, kGuardBytes, cudaMemcpyDeviceToHost));
+    for (int h = 0; h < 2; ++h)
+      for (size_t k = 0; k < kGuardBytes; ++k)
+        if (band[h][k] != kGuardByte) {
+          ++*nbad;
+          if (first.empty()) first = what + (h ? " (after its end)" : " (before its start)");
+          break;
+        }
+    return HMC_OK;
+  };
+  for (int i = 0; i < WS_COUNT; ++i) HMC_TRY(check(c->ws[i], c->ws_bytes[i], "workspace slot " + std::to_string(i)));
+  for (int i = 0; i < hmc_ctx::kBatchSlots; ++i)
+    HMC_TRY(check(c->bpool[i], c->bpool_bytes[i], "batched buffer " + std::to_string(i)));
+  if (*nbad) c->err = std::to_string(*nbad) + " guard band(s) overwritten, first: " + first;
+  return HMC_OK;
+}
+
+hmc_status hmc_guard_test_write(hmc_ctx* c) {
+  if (!c || !c->ws[WS_E]) return HMC_ERR_INVALID;
+  // one byte just past the end of the phase table: inside its guard band
+  HMC_CUDA(c, cudaMemset((unsigned char*)c->ws[WS_E] + c->ws_bytes[WS_E], 0, 1));
   return HMC_OK;
 }
 

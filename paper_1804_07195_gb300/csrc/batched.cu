@@ -480,15 +480,12 @@ static hmc_status bmalloc(hmc_ctx* c, BatchWs& w, void** p, size_t bytes) {
   const int slot = w.nalloc++;
   if (slot >= hmc_ctx::kBatchSlots) return fail(c, HMC_ERR_NOMEM, "batched workspace: too many buffers");
   if (c->bpool_bytes[slot] < bytes) {
-    if (c->bpool[slot]) cudaFree(c->bpool[slot]);
+    if (c->bpool[slot]) guarded_free(c->bpool[slot]);
     c->bpool[slot] = nullptr;
     c->bpool_bytes[slot] = 0;
-    cudaError_t e = cudaMalloc(&c->bpool[slot], bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      c->bpool[slot] = nullptr;
-      return fail(c, HMC_ERR_NOMEM, "batched workspace allocation failed");
-    }
+    void* p = nullptr;
+    if (guarded_alloc(c, bytes, &p) != HMC_OK) return fail(c, HMC_ERR_NOMEM, "batched workspace allocation failed");
+    c->bpool[slot] = p;
     c->bpool_bytes[slot] = bytes;
   }
   *p = c->bpool[slot];

@@ -213,6 +213,14 @@ hmc_status cuda_fail(hmc_ctx* c, cudaError_t e, const char* what);
 // Workspace slot of at least `bytes` bytes (grown on demand, never shrunk).
 hmc_status ws_get(hmc_ctx* c, int slot, size_t bytes, void** out);
 
+// Device buffers of the context carry guard bands: kGuardBytes before and
+// after the `bytes` the caller asked for, filled with kGuardByte. A write past
+// either end of a buffer changes a band, which hmc_check_guards reports.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+hmc_status guarded_alloc(hmc_ctx* c, size_t bytes, void** user);
+void guarded_free(void* user);
+
 // Grid size for a grid-stride kernel over `work` threads.
 inline int grid_for(const hmc_ctx* c, long long work) {
   long long g = (work + kThreads - 1) / kThreads;

@@ -155,3 +155,36 @@ def test_bounded_grid_barrier_wait_times_out_and_context_survives():
     for xs in (host(x_ref), host(x)):
         r = b - of.apply_MMdag(ol, w.phi, 0.3, xs.astype(np.complex128))
         assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b)
+
+
+def test_guard_bands_stay_intact_and_a_write_past_a_buffer_is_reported():
+    """Every device buffer of a context carries guard bands; after operator
+    applications in both designs, CG, mixed FGMRES and fCG solves, forces, a
+    trajectory and a batched solve, no band has changed. A byte written just
+    past the end of the phase table (the test hook, a plain memset inside the
+    allocation) is reported."""
+    need_gpu()
+    import paper_1804_07195_gb300 as hmc
+    w = W.small(12, 12, 16, seed=41, masses=(0.3, 1.0), U=3.0, beta=6.0)
+    with ctx_for(w.lat) as ctx:
+        phi, b = dev(w.phi), dev(w.b)
+        for v in (1, 2):
+            ctx.set_apply_variant(v)
+            ctx.apply_MMdag(phi, 0.1, b)
+            ctx.apply_MMdag(phi, 0.1, b.to(torch.complex64))
+        ctx.apply_M(phi, 0.1, b)
+        ctx.apply_Mdag(phi, 0.1, b.to(torch.complex64))
+        ctx.solve_cg(phi, 0.0, b)
+        ctx.solve_fgmres(phi, 0.2, b)
+        ctx.solve_fcg(phi, 0.2, b)
+        opts = hmc.SolverOpts(tol=1e-10)
+        chis, _ = ctx.make_chi(phi, [0.3, 1.0], [dev(r) for r in w.rho], opts=opts)
+        ctx.force(phi, [0.3, 1.0], chis, opts=opts)
+        ctx.md_trajectory(phi.clone(), dev(w.pi), [0.3, 1.0], [dev(r) for r in w.rho], hmc.Integrator(0, 4, (2, 1)),
+                          opts, opts)
+        lat = hmc.Lattice(w.lat.n, w.lat.m, w.lat.nt, w.lat.kappa, w.lat.U, w.lat.beta)
+        ctx.solve_batched([{"lattice": lat, "phi": phi, "ms": 0.1, "b": b, "x": torch.zeros_like(b)}], mixed=True)
+        assert ctx.check_guards() == 0
+        assert ctx.lib.hmc_guard_test_write(ctx.h) == 0
+        assert ctx.check_guards() == 1
+        assert b"workspace slot 0 (after its end)" in ctx.lib.hmc_last_error(ctx.h)

@@ -314,12 +314,17 @@ hmc_status hmc_md_trajectory_batched(hmc_ctx* ctx, int nchains, const hmc_chain*
  * HMC_ERR_TIMEOUT) and keeps x and its own entries of r and p in shared
  * memory. The grid-stride pair also comes with two cells per thread: the
  * neighbouring cells (i, i+1), i even, of a row, whose complex64 values are one
- * 16-byte access in every vector (n even only). variant: 0 = let the
- * autotuner choose among all of them (default), 1 = grid-stride with one
- * cell per thread, 2 = tiled only, 3 = marching only, 4 = persistent,
- * 5 = grid-stride with two cells per thread (2 to 5 fall back to variant 1
- * where they do not fit the lattice). Setting it re-runs the tuner at the
- * next FP32 solve. */
+ * 16-byte access in every vector (n even only). The sixth design runs ONE
+ * kernel and one grid-wide reduction per iteration: the single-reduction form
+ * of CG (Chronopoulos and Gear 1989; the same iterates as CG in exact
+ * arithmetic), whose kernel applies M M^dagger + sigma over tiles with
+ * M^dagger r kept in shared memory as hmc_apply_MMdag's fused kernel does,
+ * and updates x, r, p and the recurrences of w = A r and s = A p as the
+ * slices arrive. variant: 0 = let the autotuner choose among all of them
+ * (default), 1 = grid-stride with one cell per thread, 2 = tiled only,
+ * 3 = marching only, 4 = persistent, 5 = grid-stride with two cells per
+ * thread, 6 = single-reduction (2 to 6 fall back to variant 1 where they do
+ * not fit the lattice). Setting it re-runs the tuner at the next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
 /* The FP32 CG of hmc_solve_batched (mixed = 1) runs in one of two designs:
@@ -358,6 +363,16 @@ hmc_status hmc_set_fused_tile(hmc_ctx* ctx, int prec, int Ti, int Tj, int Tt, in
 /* The fused kernel's tile in use for precision prec (zeros before the first
  * fused application). */
 hmc_status hmc_fused_tile(hmc_ctx* ctx, int prec, int* Ti, int* Tj, int* Tt, int* depth, int* pairs);
+/* Pin the tile of the single-reduction FP32 CG kernel (variant 6 of
+ * hmc_set_cg_variant): Ti x Tj cells per block plus a one-cell ring
+ * ((Ti+2)(Tj+2) <= 512 threads, clamped to the lattice), Tt time slices per
+ * block, `depth` time slices staged ahead (2 or 6). All three sizes 0 return
+ * the choice to the tuner. HMC_ERR_INVALID when the tile does not fit
+ * (threads, shared memory, more blocks than the reduction buffers hold). */
+hmc_status hmc_set_cg_fused_tile(hmc_ctx* ctx, int Ti, int Tj, int Tt, int depth);
+/* The single-reduction kernel's tile and whether FP32 solves use it
+ * (in_use = 1: chosen by the tuner or pinned by variant 6). */
+hmc_status hmc_cg_fused_tile(hmc_ctx* ctx, int* Ti, int* Tj, int* Tt, int* depth, int* in_use);
 
 /* Test hook for the bounded waits of the persistent FP32 CG kernel (variant 4
  * above): from the next persistent solve on, every grid barrier waits for

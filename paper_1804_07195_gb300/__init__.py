@@ -318,7 +318,9 @@ class Context:
 
     def set_cg_variant(self, variant: int):
         """0: autotune over all FP32 CG kernel designs; 1: grid-stride; 2: tiled;
-        3: marching; 4: persistent (one cooperative launch per solve)."""
+        3: marching; 4: persistent (one cooperative launch per solve); 5:
+        grid-stride with two cells per thread; 6: single-reduction (one fused
+        kernel per iteration)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
     def set_batched_variant(self, variant: int):
@@ -351,6 +353,18 @@ class Context:
         """(Ti, Tj, Tt, depth, pairs) of the fused kernel in use for precision prec."""
         v = [C.c_int() for _ in range(5)]
         self._check(self.lib.hmc_fused_tile(self.h, prec, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def set_cg_fused_tile(self, Ti: int, Tj: int, Tt: int, depth: int = 2):
+        """Pin the single-reduction FP32 CG kernel's tile (variant 6): Ti x Tj
+        cells and Tt time slices per block, `depth` slices staged ahead (2 or
+        6); (0, 0, 0) hands the choice back to the tuner."""
+        self._check(self.lib.hmc_set_cg_fused_tile(self.h, Ti, Tj, Tt, depth))
+
+    def cg_fused_tile(self):
+        """(Ti, Tj, Tt, depth, in_use) of the single-reduction FP32 CG kernel."""
+        v = [C.c_int() for _ in range(5)]
+        self._check(self.lib.hmc_cg_fused_tile(self.h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
     def graph_mode(self) -> int:

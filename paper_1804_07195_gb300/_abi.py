@@ -116,6 +116,8 @@ PROTOTYPES = {
     "hmc_apply_variant": (S, [P, I, C.POINTER(I)]),
     "hmc_set_fused_tile": (S, [P, I, I, I, I, I, I]),
     "hmc_fused_tile": (S, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+    "hmc_set_cg_fused_tile": (S, [P, I, I, I, I]),
+    "hmc_cg_fused_tile": (S, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
     "hmc_set_wait_test": (S, [P, I, C.c_longlong]),
     "hmc_graph_mode": (S, [P, C.POINTER(I)]),
     "hmc_set_graph_mode": (S, [P, I]),

@@ -579,10 +579,11 @@ hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma,
 
 hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   if (!c) return HMC_ERR_INVALID;
-  if (variant < 0 || variant > 5) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 5");
+  if (variant < 0 || variant > 6) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 6");
   c->cg32_variant = variant;
   c->tuned32 = false;
   c->persist32 = false;
+  c->cg1_32 = false;
   destroy_graphs(c);
   return HMC_OK;
 }
@@ -634,6 +635,34 @@ hmc_status hmc_fused_tile(hmc_ctx* c, int prec, int* Ti, int* Tj, int* Tt, int* 
   *Tt = fs.Tt;
   *depth = fs.D;
   *pairs = fs.pairs;
+  return HMC_OK;
+}
+
+hmc_status hmc_set_cg_fused_tile(hmc_ctx* c, int Ti, int Tj, int Tt, int depth) {
+  if (!c) return HMC_ERR_INVALID;
+  if (Ti == 0 && Tj == 0 && Tt == 0) {  // back to the tuner
+    c->cg1_pinned = false;
+    c->tuned32 = false;
+    c->cg1_32 = false;
+    destroy_graphs(c);
+    return HMC_OK;
+  }
+  if (Ti < 1 || Tj < 1 || Tt < 1) return fail(c, HMC_ERR_INVALID, "tile sizes must be >= 1");
+  HMC_TRY(set_cg1_shape(c, Ti, Tj, Tt, depth));
+  c->tuned32 = false;
+  c->cg1_32 = false;
+  destroy_graphs(c);
+  return HMC_OK;
+}
+
+hmc_status hmc_cg_fused_tile(hmc_ctx* c, int* Ti, int* Tj, int* Tt, int* depth, int* in_use) {
+  if (!c || !Ti || !Tj || !Tt || !depth || !in_use) return HMC_ERR_INVALID;
+  const FusedShape& fs = c->cg1_shape;
+  *Ti = fs.Ti;
+  *Tj = fs.Tj;
+  *Tt = fs.Tt;
+  *depth = fs.D;
+  *in_use = c->cg1_32 ? 1 : 0;
   return HMC_OK;
 }
 

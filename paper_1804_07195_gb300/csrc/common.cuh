@@ -238,13 +238,18 @@ struct CGScal {
   int done;      // 0 running, 1 converged, 2 iteration limit, 3 breakdown (pAp <= 0 / NaN)
   int first;     // FP32 pair: no direction yet (beta = 0)
   float dm32, sigma32;  // dm and sigma rounded once for the FP32 kernels
+  // single-reduction FP32 CG: gamma = |r|^2, alpha and the iteration count,
+  // in two slots that successive launches read and write alternately
+  double cg1_gamma[2], cg1_alpha[2];
+  int cg1_it[2];
 };
 
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_TIMEOUT = 4 };
 
 // State of a grid-wide barrier between the co-resident blocks of a cooperative
-// launch: arrivals counted in `count`, release by advancing `gen`; `err` is
-// set when a wait gave up (every later barrier then returns at once).
+// launch: one arrival word, `count`, whose top bit flips each time every block
+// has arrived (`gen` is unused); `err` is set when a wait gave up (every later
+// barrier then returns at once). The host zeroes it before each launch.
 struct GridBar {
   unsigned count;
   unsigned gen;
@@ -252,27 +257,41 @@ struct GridBar {
   int pad;
 };
 
-// Barrier over all blocks of a cooperative launch. The wait of each block is
-// bounded by `limit` SM clock cycles: a block that gives up sets gb->err, and
-// every later barrier returns false at once, so the kernel can leave cleanly
-// (the host reports a timeout). Returns true when the barrier was passed.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned x) {
+  unsigned v;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "r"(x) : "memory");
+  return v;
+}
+
+// Barrier over all blocks of a cooperative launch. One atomic per block and
+// no reset: block 0 adds 2^31 - (nblocks - 1), every other block adds 1, so
+// the word grows by exactly 2^31 per barrier and its top bit changes only
+// when the last block arrives; a block waits until the top bit differs from
+// the one its own atomic returned. Its add is a release and its polls are
+// acquires, so every write before the barrier is visible after it. The wait
+// of each block is bounded by `limit` SM clock cycles: a block that gives up
+// sets gb->err, and every later barrier returns false at once, so the kernel
+// can leave cleanly (the host reports a timeout). Returns true when the
+// barrier was passed.
 __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &gb->gen;
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
     volatile int* verr = &gb->err;
     int ok = (*verr == 0);
     if (ok) {
-      const unsigned my = *vgen;
-      __threadfence();
-      if (atomicAdd(&gb->count, 1u) == nblocks - 1u) {
-        atomicExch(&gb->count, 0u);
-        __threadfence();
-        atomicAdd(&gb->gen, 1u);
-      } else {
-        const long long t0 = clock64();
-        while (*vgen == my) {
+      const bool lead = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+      __threadfence();  // the block's writes (ordered before this thread by __syncthreads) at GPU scope
+      const unsigned old = atom_add_release_gpu(&gb->count, lead ? 0x80000000u - (nblocks - 1u) : 1u);
+      const long long t0 = clock64();
+      unsigned spins = 0;
+      while (((ld_acquire_gpu(&gb->count) ^ old) & 0x80000000u) == 0u) {
+        if ((++spins & 31u) == 0u) {
           if (*verr) {
             ok = 0;
             break;
@@ -282,10 +301,8 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long
             ok = 0;
             break;
           }
-          __nanosleep(64);
         }
       }
-      __threadfence();
     }
     s_ok = ok;
   }

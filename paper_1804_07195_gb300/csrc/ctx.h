@@ -46,6 +46,7 @@ enum KernelId {
   K_CG_PERSIST32,
   K_MMDAG_FUSED32,
   K_MMDAG_FUSED64,
+  K_CG1_32,
   K_COUNT
 };
 
@@ -60,6 +61,7 @@ enum WsSlot {
   WS_U32,
   WS_CG_R64, WS_CG_P64, WS_CG_X64,
   WS_CG_R32, WS_CG_P32, WS_CG_X32, WS_CG_B32, WS_CG_Q32,
+  WS_CG1_R1, WS_CG1_W0, WS_CG1_W1, WS_CG1_S0, WS_CG1_S1,  // single-reduction FP32 CG
   WS_FG_R, WS_FG_W, WS_FG_X, WS_FG_V, WS_FG_Z,  // FGMRES vectors; V, Z hold `restart` each
   WS_F_ETA, WS_F_XI, WS_F_SRC, WS_F_TMP,        // force / action temporaries
   WS_MD_CHI, WS_MD_GRAD, WS_MD_FORCE,           // trajectory: pseudofermions, level forces
@@ -148,6 +150,9 @@ struct hmc_ctx {
   int cg32_variant = 0;  // 0 autotune over all designs, 1 grid-stride, 2 tiled, 3 marching,
                          // 4 persistent
   bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
+  bool cg1_32 = false;     // the tuner found the single-reduction FP32 CG fastest
+  bool cg1_pinned = false;  // its tile was set by the caller
+  hmc::FusedShape cg1_shape;  // tile of the single-reduction FP32 CG kernel
   // M M^dagger applications: 0 = choose per precision by timing on first use,
   // 1 = two passes (M^dagger to memory, then M), 2 = the fused kernel
   int apply_variant = 0;

@@ -97,9 +97,6 @@ __device__ __forceinline__ void st_c(V2<R>* s, int k, Cx<R> v) {
 
 }  // namespace
 
-template <int J>
-using IC = std::integral_constant<int, J>;
-
 // out = (M M^dagger + sigma) p over the tile of this block; see the header
 // comment. ph: the phase source (phi as float for R = float, the table
 // e^{i phi} for R = double), in the canonical layout.

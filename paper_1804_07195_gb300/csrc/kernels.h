@@ -2,6 +2,8 @@
 // enqueues on ctx->stream and returns a status; none synchronises.
 #pragma once
 
+#include <functional>
+
 #include "ctx.h"
 
 namespace hmc {
@@ -30,6 +32,28 @@ bool fused_ok(const Geo& g, const FusedShape& fs);
 // two-cells-per-thread kernel (pairs) for prec 32 or 64; HMC_ERR_INVALID if
 // it does not fit.
 hmc_status set_fused_shape(hmc_ctx* c, int prec, int Ti, int Tj, int Tt, int D, int pairs);
+
+// Single-reduction FP32 CG (cg32_fused.cu): one launch per iteration over
+// tiles of the fused M M^dagger kernel. Buffers: r, w, s alternate between
+// two vectors (r[0] is the solve's residual vector), the partials between
+// partA and partB.
+struct CG1Bufs {
+  float2* r[2];
+  float2* w[2];
+  float2* s[2];
+  float2* part[2];
+};
+// Workspace vectors of the buffers (r[1] == nullptr when one cannot be had).
+CG1Bufs cg1_bufs(hmc_ctx* c, float2* r0);
+bool cg1_ok(const hmc_ctx* c, const Geo& g, const FusedShape& fs);
+// w_0 = A r_0 and the partials of gamma_0, delta_0 (after the CG state was initialised)
+hmc_status cg1_prime_launch(hmc_ctx* c, const Geo& g, const CG1Bufs& B, float2* p, float2* x, CGScal* sc);
+// iteration with state slot par (successive iterations alternate 0, 1)
+hmc_status cg1_iter_launch(hmc_ctx* c, const Geo& g, const CG1Bufs& B, float2* p, float2* x, CGScal* sc, int par);
+// Tile tuner; reinit re-initialises the CG state before each candidate.
+bool cg1_tune(hmc_ctx* c, const Geo& g, const CG1Bufs& B, float2* p, float2* x, CGScal* sc,
+              const std::function<hmc_status()>& reinit);
+hmc_status set_cg1_shape(hmc_ctx* c, int Ti, int Tj, int Tt, int D);
 
 // CG building blocks on the state sc (see common.cuh).
 template <typename R>

@@ -2,6 +2,8 @@
 // the context's current field, and launches with programmatic dependent launch.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "operator.cuh"
 
@@ -24,11 +26,12 @@ inline Phase<float> phase_of<float>(hmc_ctx* c) {
 // captured iteration chunk: the first kernel of a capture (no kernel before it
 // in the graph) and every launch outside a capture are ordinary launches.
 template <typename... KA, typename... A>
-inline void launch_pdl(hmc_ctx* c, void (*k)(KA...), dim3 grid, int threads, cudaStream_t s, A... args) {
+inline void launch_pdl_smem(hmc_ctx* c, void (*k)(KA...), dim3 grid, int threads, int smem, cudaStream_t s,
+                            A... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -39,5 +42,12 @@ inline void launch_pdl(hmc_ctx* c, void (*k)(KA...), dim3 grid, int threads, cud
   (void)cudaLaunchKernelEx(&cfg, k, ((KA)args)...);  // errors surface through cudaGetLastError
   if (c->capturing) c->pdl_armed = true;
 }
+template <typename... KA, typename... A>
+inline void launch_pdl(hmc_ctx* c, void (*k)(KA...), dim3 grid, int threads, cudaStream_t s, A... args) {
+  launch_pdl_smem(c, k, grid, threads, 0, s, args...);
+}
+
+template <int J>
+using IC = std::integral_constant<int, J>;
 
 }  // namespace hmc

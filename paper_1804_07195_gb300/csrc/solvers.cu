@@ -151,14 +151,41 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
     }
   }
   for (int k = 0; k < nk; ++k) c->shape[ids[k]] = keep[k];
-  // FP32: the persistent kernel against the chosen pair, both through the
-  // solver path they would run in (48 iterations, twice each, best kept)
+  // FP32: the single-reduction kernel's tile (variants 0 and 6), then the
+  // designs against each other through the solver path they would run in
+  // (48 iterations, twice each, best kept): the chosen pair, the persistent
+  // kernel, the single-reduction kernel
   if constexpr (sizeof(R) == 4) {
     c->persist32 = false;
-    if (c->cg32_variant == 0 && !c->capturing && cg32_persist_ok(c, g)) {
-      float tm[2] = {1e30f, 1e30f};
-      for (int k = 0; k < 2; ++k) {
-        c->persist32 = (k == 1);
+    c->cg1_32 = false;
+    bool cg1_fit = false;
+    if ((var == 0 || var == 6) && !c->capturing) {
+      const CG1Bufs B = cg1_bufs(c, (float2*)r);
+      if (B.r[1] != nullptr) {
+        if (c->cg1_pinned)
+          cg1_fit = cg1_ok(c, g, c->cg1_shape);
+        else
+          cg1_fit = cg1_tune(c, g, B, (float2*)p, (float2*)x, sc, [&] {
+            return init0_launch<R>(c, g.N, b, x, r, p, sc, 0.0, 1 << 30, sigma, tk, c->delta * ms);
+          });
+      }
+      HMC_CUDA(c, cudaGetLastError());
+      c->err.clear();
+    }
+    if (var == 6) c->cg1_32 = cg1_fit;
+    if (var == 0 && !c->capturing) {
+      struct Design {
+        bool persist, cg1;
+      };
+      std::vector<Design> designs = {{false, false}};
+      if (cg32_persist_ok(c, g)) designs.push_back({true, false});
+      if (cg1_fit) designs.push_back({false, true});
+      float best_t = 1e30f;
+      Design best_d = designs[0];
+      for (size_t k = 0; designs.size() > 1 && k < designs.size(); ++k) {
+        c->persist32 = designs[k].persist;
+        c->cg1_32 = designs[k].cg1;
+        float tm = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
           SolveStats tmp;
           HMC_CUDA(c, cudaEventRecord(e0, c->stream));
@@ -167,6 +194,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           HMC_CUDA(c, cudaEventSynchronize(e1));
           if (st != HMC_OK && st != HMC_ERR_NOT_CONVERGED) {
             c->persist32 = false;
+            c->cg1_32 = false;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return st;
@@ -174,10 +202,15 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           c->err.clear();
           float t = 0.f;
           cudaEventElapsedTime(&t, e0, e1);
-          tm[k] = std::min(tm[k], t);
+          tm = std::min(tm, t);
+        }
+        if (tm < best_t) {
+          best_t = tm;
+          best_d = designs[k];
         }
       }
-      c->persist32 = tm[1] < tm[0];
+      c->persist32 = best_d.persist;
+      c->cg1_32 = best_d.cg1;
     }
   }
   cudaEventDestroy(e0);
@@ -211,9 +244,15 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   V2<R>* q = nullptr;
   if (sizeof(R) == 4)
     HMC_TRY(ws_get(c, WS_CG_Q32, sizeof(V2<R>) * (size_t)g.N, (void**)&q));
+  bool single = false;  // FP32 single-reduction design (decided below)
+  CG1Bufs B{};
   auto iterate = [&](int n) -> hmc_status {
     for (int i = 0; i < n; ++i) {
       if constexpr (sizeof(R) == 4) {
+        if (single) {
+          HMC_TRY(cg1_iter_launch(c, g, B, (float2*)p, (float2*)x, sc, i & 1));
+          continue;
+        }
         float2* pold = (i & 1) ? (float2*)q : (float2*)p;
         float2* pnew = (i & 1) ? (float2*)p : (float2*)q;
         HMC_TRY(cg32_pmdag_launch(c, g, (const float2*)r, pold, pnew, (float2*)u, sc, tk));
@@ -243,17 +282,33 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
       c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
     }
   }
-  const int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64,
-                      K_CG_P64};
-  const double kbytes[3] = {sizeof(R) == 4 ? 36.0 : 48.0, sizeof(R) == 4 ? 52.0 : 112.0, 48.0};
-  const int nk = sizeof(R) == 4 ? 2 : 3;
+  // FP32: one single-reduction launch per iteration when the tuner (or the
+  // pinned variant) chose it; it starts from w_0 = A r_0
+  if constexpr (sizeof(R) == 4) {
+    single = !persistent && (c->cg32_variant == 0 || c->cg32_variant == 6) && c->cg1_32 &&
+             cg1_ok(c, g, c->cg1_shape);
+    if (single) {
+      B = cg1_bufs(c, (float2*)r);
+      if (B.r[1] == nullptr) return fail(c, HMC_ERR_NOMEM, "single-reduction CG vectors");
+      HMC_TRY(cg1_prime_launch(c, g, B, (float2*)p, (float2*)x, sc));
+      st->applies32++;
+    }
+  }
+  int kid[3] = {sizeof(R) == 4 ? K_CG_MDAG32 : K_CG_MDAG64, sizeof(R) == 4 ? K_CG_M32 : K_CG_M64, K_CG_P64};
+  double kbytes[3] = {sizeof(R) == 4 ? 36.0 : 48.0, sizeof(R) == 4 ? 52.0 : 112.0, 48.0};
+  int nk = sizeof(R) == 4 ? 2 : 3;
+  if (single) {
+    kid[0] = K_CG1_32;
+    kbytes[0] = kKernelBytesPerSite[K_CG1_32];
+    nk = 1;
+  }
   // The whole solve as one graph launch: chunks of kChunk iterations repeated
   // by a device-side while loop until the done flag is set (or the trip bound,
   // maxit / kChunk + 2, is reached); the host waits once, at the end.
   bool looped = false;
   if (!persistent && c->use_graphs && c->use_loop_graphs && !c->prof.timing && !c->capturing) {
     const void* key[6] = {sc, r, p, q, u, x};
-    const int kind = (sizeof(R) == 4 ? 32 : 64) + 1000;
+    const int kind = (sizeof(R) == 4 ? 32 : 64) + 1000 + (single ? 500 : 0);
     GraphEntry* le = find_graph(c, kind, key);
     if (!le) {
       cudaGraphExec_t exec;
@@ -290,7 +345,7 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   GraphEntry* ge = nullptr;
   if (!persistent && !looped && c->use_graphs && !c->prof.timing) {
     const void* key[6] = {sc, r, p, q, u, x};
-    const int kind = sizeof(R) == 4 ? 32 : 64;
+    const int kind = (sizeof(R) == 4 ? 32 : 64) + (single ? 500 : 0);
     ge = find_graph(c, kind, key);
     if (!ge) {
       cudaGraphExec_t exec;

@@ -237,9 +237,10 @@ def main():
                     help="inner tolerance factor a of Algorithm A.1 for the trajectory's solves "
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
-    ap.add_argument("--cg-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
-                    help="FP32 CG design of the trajectory's context: 0 = autotuned (default); 1-4 pin "
-                         "grid-stride, tiled, marching or persistent (hmc_set_cg_variant). Under a "
+    ap.add_argument("--cg-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+                    help="FP32 CG design of the trajectory's context: 0 = autotuned (default); 1-6 pin "
+                         "grid-stride, tiled, marching, persistent, grid-stride with two cells per "
+                         "thread or single-reduction (hmc_set_cg_variant). Under a "
                          "profiler the autotuner's timings are distorted, so launch lists pin the design "
                          "the tuner chooses without one.")
     ap.add_argument("--graph-mode", type=int, default=2, choices=[1, 2],
@@ -247,11 +248,20 @@ def main():
                          "chunks with host checks, the mode kernel profilers can see into")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs",
+                             "spcg_single",
                              "mmdag32_stream", "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64",
                              "batched", "force", "md_short", "trajectory"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
+    ap.add_argument("--write-traffic", default=None, metavar="CSV",
+                    help="write profiles/traffic.json from the raw-page CSV of an ncu capture of the FP32 "
+                         "CG kernels (ncu -i REPORT --page raw --csv --print-units base > CSV) and exit")
+    ap.add_argument("--traffic-command", default="",
+                    help="the ncu command that made the report (recorded with the traffic)")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.traffic_command)
+        return
     ws, rank, local = dist_env()
     if args.kernel_case:
         kernel_case(args.kernel_case, args.graph_mode, args.cg_variant, args.fgmres_a)
@@ -370,15 +380,16 @@ def main():
     achieved = bytes_launch / avg_s / 1e9 if avg_s > 0 else 0.0
     tot_prof_ms = sum(v["ms"] for v in prof.values())
     traffic = None
+    dfunc = TRAFFIC_FUNCS.get((dname, dstat.get("design", 0)))
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
-        if tj.get("source_sha") == kernel_source_sha() and dname in tj.get("kernels", {}):
-            traffic = tj["kernels"][dname]
+        if tj.get("source_sha") == kernel_source_sha() and dfunc in tj.get("kernels", {}):
+            traffic = tj["kernels"][dfunc]
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": dname,
+                "frac": achieved / hbm, "traffic": traffic, "kernel": dname, "function": dfunc,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "launches_per_step": dstat["launches"], "avg_launch_us": avg_s * 1e6,
                 "share_of_kernel_time": dstat["ms"] / tot_prof_ms if tot_prof_ms else None,
@@ -447,12 +458,12 @@ def main():
         torch.cuda.synchronize()
         solve[name] = {"ms": a.elapsed_time(z), "iters": info["iters"], "inner_iters": info["iters_inner"],
                        "restarts": info["iters_outer"], "true_rel_res": info["true_rel_res"]}
-    # the two FP32 CG kernel designs, each pinned in its own context: 300
+    # the FP32 CG kernel designs, each pinned in its own context: 300
     # iterations of single-precision CG (no convergence test reached)
     designs = {}
     with hmc.Context(lat) as c2:
         for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3), ("persistent", 4),
-                         ("grid_stride_two_cells", 5)):
+                         ("grid_stride_two_cells", 5), ("single_reduction", 6)):
             c2.set_cg_variant(v)
             b32 = b.to(torch.complex64)
             c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
@@ -467,6 +478,8 @@ def main():
             designs[vname] = {"ms": a.elapsed_time(z), "iters": info["iters"],
                               "us_per_iter": 1e3 * a.elapsed_time(z) / max(info["iters"], 1),
                               "shape": {"threads": sh["threads"], "waves": sh["waves"], "design": sh["design"]}}
+            if v == 6:
+                designs[vname]["shape"] = dict(zip(("Ti", "Tj", "Tt", "depth", "in_use"), c2.cg_fused_tile()))
     solve["fp32_cg_designs"] = designs
     # the pair as production runs it (graph replay, no per-launch events): one
     # FP32 CG iteration moves 36 + 52 = 88 algorithmic bytes per site
@@ -853,9 +866,9 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
         ctx.set_graph_mode(graph_mode)
-        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs"):
+        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs", "spcg_single"):
             ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
-                                "spcg_persist": 4, "spcg_pairs": 5}[case])
+                                "spcg_persist": 4, "spcg_pairs": 5, "spcg_single": 6}[case])
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)
@@ -904,12 +917,17 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
 # fused M M^dagger tile of the streaming kernel profile: Ti, Tj, Tt, depth, pairs
 FUSED_STREAM_TILE = (28, 6, 64, 2, 1)
 
-# the translation unit of the FP32 CG pair (the kernels whose DRAM traffic
-# profiles/traffic.json records): kernels.cu and everything it includes
-PAIR_SOURCES = ("paper_1804_07195_gb300/csrc/kernels.cu", "paper_1804_07195_gb300/csrc/kernels.h",
-                "paper_1804_07195_gb300/csrc/ctx.h", "paper_1804_07195_gb300/csrc/common.cuh",
-                "paper_1804_07195_gb300/csrc/operator.cuh", "paper_1804_07195_gb300/csrc/launch.cuh",
-                "include/hmc.h")
+# the translation units of the FP32 CG kernels whose DRAM traffic
+# profiles/traffic.json records, and everything they include
+PAIR_SOURCES = ("paper_1804_07195_gb300/csrc/kernels.cu", "paper_1804_07195_gb300/csrc/cg32_fused.cu",
+                "paper_1804_07195_gb300/csrc/kernels.h", "paper_1804_07195_gb300/csrc/ctx.h",
+                "paper_1804_07195_gb300/csrc/common.cuh", "paper_1804_07195_gb300/csrc/operator.cuh",
+                "paper_1804_07195_gb300/csrc/launch.cuh", "include/hmc.h")
+
+# (profile name, design) of a CG kernel -> its CUDA function
+TRAFFIC_FUNCS = {("cg_pMdag_f32", 0): "k_cg32_pmdag", ("cg_M_update_f32", 0): "k_cg32_m",
+                 ("cg_pMdag_f32", 4): "k_cg32_pmdag2", ("cg_M_update_f32", 4): "k_cg32_m2",
+                 ("cg1_fused_f32", 0): "k_cg32_fused1"}
 
 
 def kernel_source_sha():
@@ -918,6 +936,41 @@ def kernel_source_sha():
     for f in PAIR_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def traffic_from_csv(text):
+    """Mean DRAM bytes (read + written) per launch of every kernel in the
+    raw-page CSV of an ncu report printed with base units, and the launch
+    counts: ({function: bytes}, {function: launches})."""
+    import csv
+    import re
+    rows = list(csv.reader(text.splitlines()))
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr, units = rows[start], rows[start + 1]
+    ki, ri, wi = hdr.index("Kernel Name"), hdr.index("dram__bytes_read.sum"), hdr.index("dram__bytes_write.sum")
+    if units[ri] != "byte" or units[wi] != "byte":
+        raise ValueError(f"expected base units (byte), got {units[ri]!r}, {units[wi]!r}")
+    per = {}
+    for r in rows[start + 2:]:
+        if len(r) != len(hdr):
+            continue
+        m = re.search(r"\b(k_\w+)", r[ki])
+        if not m:
+            continue
+        per.setdefault(m.group(1), []).append(float(r[ri].replace(",", "")) + float(r[wi].replace(",", "")))
+    return {k: sum(v) / len(v) for k, v in per.items()}, {k: len(v) for k, v in per.items()}
+
+
+def write_traffic(csv_path, command):
+    with open(csv_path) as f:
+        kernels, launches = traffic_from_csv(f.read())
+    rec = {"source_sha": kernel_source_sha(), "sources": list(PAIR_SOURCES), "capture": command,
+           "kernels": kernels, "launches_captured": launches,
+           "note": "cold-cache DRAM bytes read + written per launch (caches flushed before each ncu pass)"}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec))
 
 
 if __name__ == "__main__":

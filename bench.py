@@ -915,7 +915,7 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
 
 
 # fused M M^dagger tile of the streaming kernel profile: Ti, Tj, Tt, depth, pairs
-FUSED_STREAM_TILE = (28, 6, 64, 2, 1)
+FUSED_STREAM_TILE = (28, 14, 22, 2, 1)
 
 # the translation units of the FP32 CG kernels whose DRAM traffic
 # profiles/traffic.json records, and everything they include

@@ -333,6 +333,40 @@ __device__ __forceinline__ Cx<float> lo_c(const float4& v) { return Cx<float>{v.
 __device__ __forceinline__ Cx<float> hi_c(const float4& v) { return Cx<float>{v.z, v.w}; }
 __device__ __forceinline__ float4 pack4(Cx<float> a, Cx<float> b) { return make_float4(a.re, a.im, b.re, b.im); }
 
+// Packed FP32 pair arithmetic (add.rn.f32x2, fma.rn.f32x2; sm_100 and
+// later): each lane is rounded as the scalar instruction would round it, so
+// a sum formed this way equals the scalar one bit for bit.
+__device__ __forceinline__ unsigned long long pk2(Cx<float> v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.re), "f"(v.im));
+  return r;
+}
+__device__ __forceinline__ Cx<float> upk2(unsigned long long v) {
+  Cx<float> r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.re), "=f"(r.im) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long add_x2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma_x2(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// hopsum with both components in one packed pair: t - dk (a + b + c);
+// ndk = (-dk, -dk)
+__device__ __forceinline__ Cx<float> hopsum_x2(Cx<float> t, unsigned long long ndk, Cx<float> a, Cx<float> b,
+                                               Cx<float> c) {
+  return upk2(fma_x2(ndk, add_x2(add_x2(pk2(a), pk2(b)), pk2(c)), pk2(t)));
+}
+// (re, im) of the pair's first and second cell
+__device__ __forceinline__ Cx<float> hi_of(const float4* v) { return Cx<float>{v->z, v->w}; }
+__device__ __forceinline__ Cx<float> lo_of(const float4* v) { return Cx<float>{v->x, v->y}; }
+
 // At most 256 threads per block and 80 registers per thread: six blocks of
 // 128 threads share an SM.
 constexpr int kPairMaxThreads = 256;
@@ -416,6 +450,7 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
 
   float4 pAc{}, pBc{}, uA_prev{}, uB_cur{};
   Cx<float> ea_c0{}, ea_c1{};
+  const unsigned long long ndk = pk2(Cx<float>{-dk, -dk});
   int toff_out = t0 * V;
 
   auto step = [&](auto JJ, auto OUTC, int k) {
@@ -443,21 +478,25 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
     }
     if (need_uA) {
       // u_A(t) = -p_A(t) + (e^{-i phi_A(t+1)} - dm) p_A(t+1) - dk [p_B(i,j) + p_B(i-1,j) + p_B(i,j-1)](t)
-      const float4 left = SB[J * NT + nim], up = SB[J * NT + njm];
-      const Cx<float> u0 = hopsum(cfma(Cx<float>{ea_n0.re - dm, -ea_n0.im}, lo_c(pAn), Cx<float>{-pAc.x, -pAc.y}),
-                                  dk, lo_c(pBc), hi_c(left), lo_c(up));
-      const Cx<float> u1 = hopsum(cfma(Cx<float>{ea_n1.re - dm, -ea_n1.im}, hi_c(pAn), Cx<float>{-pAc.z, -pAc.w}),
-                                  dk, hi_c(pBc), lo_c(pBc), hi_c(up));
+      // (of the left pair only its second cell is read)
+      const Cx<float> left = hi_of(SB + J * NT + nim);
+      const float4 up = SB[J * NT + njm];
+      const Cx<float> u0 = hopsum_x2(cfma(Cx<float>{ea_n0.re - dm, -ea_n0.im}, lo_c(pAn), Cx<float>{-pAc.x, -pAc.y}),
+                                     ndk, lo_c(pBc), left, lo_c(up));
+      const Cx<float> u1 = hopsum_x2(cfma(Cx<float>{ea_n1.re - dm, -ea_n1.im}, hi_c(pAn), Cx<float>{-pAc.z, -pAc.w}),
+                                     ndk, hi_c(pBc), lo_c(pBc), hi_c(up));
       uA = pack4(u0, u1);
       UA[tid] = uA;
     }
     if (need_uB) {
       // u_B(t+1) = p_B(t+1) + (dm - e^{i phi_B(t)}) p_B(t) - dk [p_A(i,j) + p_A(i+1,j) + p_A(i,j+1)](t+1)
-      const float4 right = SA[JN * NT + nip], down = SA[JN * NT + njp];
-      const Cx<float> u0 = hopsum(cfma(Cx<float>{dm - eb_c0.re, -eb_c0.im}, lo_c(pBc), lo_c(pBn)), dk, lo_c(pAn),
-                                  hi_c(pAn), lo_c(down));
-      const Cx<float> u1 = hopsum(cfma(Cx<float>{dm - eb_c1.re, -eb_c1.im}, hi_c(pBc), hi_c(pBn)), dk, hi_c(pAn),
-                                  lo_c(right), hi_c(down));
+      // (of the right pair only its first cell is read)
+      const Cx<float> right = lo_of(SA + JN * NT + nip);
+      const float4 down = SA[JN * NT + njp];
+      const Cx<float> u0 = hopsum_x2(cfma(Cx<float>{dm - eb_c0.re, -eb_c0.im}, lo_c(pBc), lo_c(pBn)), ndk, lo_c(pAn),
+                                     hi_c(pAn), lo_c(down));
+      const Cx<float> u1 = hopsum_x2(cfma(Cx<float>{dm - eb_c1.re, -eb_c1.im}, hi_c(pBc), hi_c(pBn)), ndk,
+                                     hi_c(pAn), right, hi_c(down));
       uBn = pack4(u0, u1);
       UB[((J + 1) & 1) * NT + tid] = uBn;
     }
@@ -465,17 +504,19 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
       __syncthreads();
       if (in_tile) {
         const float4* UBc = UB + (J & 1) * NT;
-        const float4 bl = UBc[nim], bu = UBc[njm], ar = UA[nip], ad = UA[njp];
+        // of the left pair only its second cell, of the right pair only its first is read
+        const Cx<float> bl = hi_of(UBc + nim), ar = lo_of(UA + nip);
+        const float4 bu = UBc[njm], ad = UA[njp];
         // (M u)_A(t) = -u_A(t) + (e^{i phi_A(t)} - dm) u_A(t-1) - dk [u_B(i,j) + u_B(i-1,j) + u_B(i,j-1)](t)
-        Cx<float> oA0 = hopsum(cfma(Cx<float>{ea_c0.re - dm, ea_c0.im}, lo_c(uA_prev), Cx<float>{-uA.x, -uA.y}), dk,
-                               lo_c(uB_cur), hi_c(bl), lo_c(bu));
-        Cx<float> oA1 = hopsum(cfma(Cx<float>{ea_c1.re - dm, ea_c1.im}, hi_c(uA_prev), Cx<float>{-uA.z, -uA.w}), dk,
-                               hi_c(uB_cur), lo_c(uB_cur), hi_c(bu));
+        Cx<float> oA0 = hopsum_x2(cfma(Cx<float>{ea_c0.re - dm, ea_c0.im}, lo_c(uA_prev), Cx<float>{-uA.x, -uA.y}),
+                                  ndk, lo_c(uB_cur), bl, lo_c(bu));
+        Cx<float> oA1 = hopsum_x2(cfma(Cx<float>{ea_c1.re - dm, ea_c1.im}, hi_c(uA_prev), Cx<float>{-uA.z, -uA.w}),
+                                  ndk, hi_c(uB_cur), lo_c(uB_cur), hi_c(bu));
         // (M u)_B(t) = u_B(t) + (dm - e^{-i phi_B(t)}) u_B(t+1) - dk [u_A(i,j) + u_A(i+1,j) + u_A(i,j+1)](t)
-        Cx<float> oB0 = hopsum(cfma(Cx<float>{dm - eb_c0.re, eb_c0.im}, lo_c(uBn), lo_c(uB_cur)), dk, lo_c(uA),
-                               hi_c(uA), lo_c(ad));
-        Cx<float> oB1 = hopsum(cfma(Cx<float>{dm - eb_c1.re, eb_c1.im}, hi_c(uBn), hi_c(uB_cur)), dk, hi_c(uA),
-                               lo_c(ar), hi_c(ad));
+        Cx<float> oB0 = hopsum_x2(cfma(Cx<float>{dm - eb_c0.re, eb_c0.im}, lo_c(uBn), lo_c(uB_cur)), ndk, lo_c(uA),
+                                  hi_c(uA), lo_c(ad));
+        Cx<float> oB1 = hopsum_x2(cfma(Cx<float>{dm - eb_c1.re, eb_c1.im}, hi_c(uBn), hi_c(uB_cur)), ndk, hi_c(uA),
+                                  ar, hi_c(ad));
         float4 oA = pack4(oA0, oA1), oB = pack4(oB0, oB1);
         oA.x = fmaf(sigma, pAc.x, oA.x);
         oA.y = fmaf(sigma, pAc.y, oA.y);
@@ -633,10 +674,13 @@ static hmc_status tune_fused(hmc_ctx* c, const Geo& g, R dm, R sigma, const V2<R
   c->fused_tuned[pi] = true;
   std::vector<FusedShape> cands;
   const bool aligned16 = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  // time ranges: short ones, and the lattice's time extent in one, two or
+  // three parts (whichever fills the SMs' block slots best)
+  const int tts[6] = {4, 8, 16, (g.nt + 2) / 3, (g.nt + 1) / 2, g.nt};
   for (int pairs : {1, 0})
     for (int TX : {16, 32, 64})
-      for (int Tj : {4, 6, 8, 14, 30})
-        for (int Tt : {4, 8, 16, 64})
+      for (int Tj : {4, 6, 8, 10, 14, 30})
+        for (int Tt : tts)
           for (int D : {2, 6}) {
             if (pairs && !aligned16) continue;
             if (!pairs && TX == 16) continue;

@@ -253,11 +253,11 @@ def main():
                              "batched", "force", "md_short", "trajectory"],
                     help="run one solve or application on the benchmark lattice and exit "
                          "(the small case for kernel profiles)")
-    ap.add_argument("--write-traffic", default=None, metavar="CSV",
-                    help="write profiles/traffic.json from the raw-page CSV of an ncu capture of the FP32 "
+    ap.add_argument("--write-traffic", default=None, nargs="+", metavar="CSV",
+                    help="write profiles/traffic.json from the raw-page CSVs of ncu captures of the FP32 "
                          "CG kernels (ncu -i REPORT --page raw --csv --print-units base > CSV) and exit")
-    ap.add_argument("--traffic-command", default="",
-                    help="the ncu command that made the report (recorded with the traffic)")
+    ap.add_argument("--traffic-command", default=[], action="append",
+                    help="an ncu command that made one of the reports (recorded with the traffic)")
     args = ap.parse_args()
     if args.write_traffic:
         write_traffic(args.write_traffic, args.traffic_command)
@@ -869,6 +869,8 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
         if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs", "spcg_single"):
             ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
                                 "spcg_persist": 4, "spcg_pairs": 5, "spcg_single": 6}[case])
+            if case == "spcg_single":
+                ctx.set_cg_fused_tile(*SINGLE_REDUCTION_TILE)
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)
         elif case == "cg64":
             _, info = ctx.solve_cg(phi, 0.0, b, tol=1e-10, maxit=30, allow_fail=True)
@@ -913,6 +915,10 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
         torch.cuda.synchronize()
     print(json.dumps({"case": case, **{k: v for k, v in info.items()}}))
 
+
+# tile of the single-reduction CG kernel profile (the tuner's choice on the
+# 102x102x64 lattice): Ti, Tj, Tt, depth
+SINGLE_REDUCTION_TILE = (14, 8, 16, 2)
 
 # fused M M^dagger tile of the streaming kernel profile: Ti, Tj, Tt, depth, pairs
 FUSED_STREAM_TILE = (28, 14, 22, 2, 1)
@@ -961,10 +967,14 @@ def traffic_from_csv(text):
     return {k: sum(v) / len(v) for k, v in per.items()}, {k: len(v) for k, v in per.items()}
 
 
-def write_traffic(csv_path, command):
-    with open(csv_path) as f:
-        kernels, launches = traffic_from_csv(f.read())
-    rec = {"source_sha": kernel_source_sha(), "sources": list(PAIR_SOURCES), "capture": command,
+def write_traffic(csv_paths, commands):
+    kernels, launches = {}, {}
+    for path in csv_paths:
+        with open(path) as f:
+            k, n = traffic_from_csv(f.read())
+        kernels.update(k)
+        launches.update(n)
+    rec = {"source_sha": kernel_source_sha(), "sources": list(PAIR_SOURCES), "capture": commands,
            "kernels": kernels, "launches_captured": launches,
            "note": "cold-cache DRAM bytes read + written per launch (caches flushed before each ncu pass)"}
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:

@@ -34,3 +34,17 @@ def test_every_traffic_function_has_a_profile_name():
     assert set(bench.TRAFFIC_FUNCS.values()) >= {"k_cg32_pmdag", "k_cg32_m", "k_cg32_fused1"}
     for f in bench.PAIR_SOURCES:
         assert os.path.exists(os.path.join(bench.ROOT, f)), f
+
+
+def test_write_traffic_merges_reports(tmp_path, monkeypatch):
+    a, b = tmp_path / "a.csv", tmp_path / "b.csv"
+    a.write_text(CSV)
+    b.write_text(CSV.replace("k_cg32_pmdag", "k_cg32_fused1").replace("k_cg32_m(", "k_cg32_m2("))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0123456789abcdef")
+    (tmp_path / "profiles").mkdir()
+    bench.write_traffic([str(a), str(b)], ["ncu A", "ncu B"])
+    import json
+    rec = json.loads((tmp_path / "profiles" / "traffic.json").read_text())
+    assert set(rec["kernels"]) == {"k_cg32_pmdag", "k_cg32_m", "k_cg32_fused1", "k_cg32_m2"}
+    assert rec["source_sha"] == "0123456789abcdef" and rec["capture"] == ["ncu A", "ncu B"]

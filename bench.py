@@ -514,8 +514,23 @@ def main():
     chis_f, _ = ctx.make_chi(phi0, masses, rho_s, opts=hmc.SolverOpts(method=0, tol=1e-14))
     S12, _ = ctx.action(phi_f, masses, chis_f, opts=act_opts)
     S14, _ = ctx.action(phi_f, masses, chis_f, opts=hmc.SolverOpts(method=0, tol=1e-14))
+    # a-posteriori bound of the action error of solves at the action
+    # tolerance: for S_i = src_i^dagger eta_i with A eta_i = src_i, a computed
+    # eta with true residual r gives |dS_i| <= |eta| |r| (Section 5.1's terms:
+    # src_i = M_{mu_i} chi_i on M_{mu_{i-1}}, the top term chi_n on M_{mu_{n-1}})
+    bound_terms = []
+    for i in range(len(masses) + 1):
+        lo = 0.0 if i == 0 else masses[i - 1]
+        src = chis_f[i] if i == len(masses) else ctx.apply_M(phi_f, masses[i], chis_f[i])
+        eta, _ = ctx.solve_fgmres(phi_f, lo, src, tol=1e-12, a=args.fgmres_a)
+        r = src - ctx.apply_MMdag(phi_f, lo, eta)
+        bound_terms.append(float(torch.linalg.vector_norm(eta)) * float(torch.linalg.vector_norm(r)))
     dH_check = {"dH_mixed": float(dH[0]), "dH_fp64": H1f - H0f, "abs_difference": abs(H1f - H0f - dH[0]),
                 "action_true_rel_res_fp64": info_f["true_rel_res"],
+                "action_error_bound_at_1e-12": {"terms": bound_terms, "sum": sum(bound_terms),
+                                                "note": "|eta| |r| per Hasenbusch term for mixed solves at "
+                                                        "1e-12 on this trajectory's final field: bounds the "
+                                                        "action error those solves put into H1"},
                 "action_error_at_1e-12": {"S_mixed_1e-12": S12, "S_fp64_1e-14": S14, "abs_difference": abs(S12 - S14),
                                           "note": "the action at the end of this trajectory from the bench's "
                                                   "action solves (mixed, 1e-12) against FP64 CG at 1e-14: what "

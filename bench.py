@@ -156,7 +156,10 @@ def cpu_oracle_cg(iters: int):
 
 def _c3_oracle_job(q):
     """(In a spawned process) the oracle's FP64 CG on the 36x36x64 system
-    (m_s = 0) to 1e-12, timed."""
+    (m_s = 0) to 1e-12, timed, on the last host core only."""
+    if hasattr(os, "sched_setaffinity"):
+        cores = sorted(os.sched_getaffinity(0))
+        os.sched_setaffinity(0, {cores[-1]})
     import workloads as W
     from oracle import fermion, solvers
     from oracle.lattice import Lattice
@@ -176,7 +179,19 @@ def start_c3_oracle():
     mctx = mp.get_context("spawn")
     q = mctx.Queue()
     proc = mctx.Process(target=_c3_oracle_job, args=(q,), daemon=True)
-    proc.start()
+    # one thread in every numerical library of the child (the environment is
+    # copied when it starts), so it leaves the other cores to the launches
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        proc.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return proc, q
 
 
@@ -620,6 +635,12 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                         fn()
                     torch.cuda.synchronize()
                     reps = 20
+                    # a head start of GPU work, so that the host has queued
+                    # every timed application before the GPU reaches it (the
+                    # events around each launch would otherwise include any
+                    # host delay between them)
+                    for _ in range(32):
+                        flush.zero_()
                     ctx.profile(True, reset=True)
                     for _ in range(reps):
                         if name.startswith("streaming"):

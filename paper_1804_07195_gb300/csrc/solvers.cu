@@ -128,6 +128,10 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
         }
   float best = 1e30f;
   Shape keep[3];
+  // the fastest shape of each kernel family (tiled: 0 grid-stride, 1 tiled,
+  // 2 marching, 4 grid-stride with two cells per thread)
+  float fam_t[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+  Shape fam[5][3];
   for (const Shape& cand : cands) {
     {
       for (int k = 0; k < nk; ++k) {
@@ -148,13 +152,20 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
         best = ms_;
         for (int k = 0; k < nk; ++k) keep[k] = c->shape[ids[k]];
       }
+      const int f = cand.tiled;
+      if (f >= 0 && f < 5 && ms_ < fam_t[f]) {
+        fam_t[f] = ms_;
+        for (int k = 0; k < nk; ++k) fam[f][k] = c->shape[ids[k]];
+      }
     }
   }
   for (int k = 0; k < nk; ++k) c->shape[ids[k]] = keep[k];
   // FP32: the single-reduction kernel's tile (variants 0 and 6), then the
   // designs against each other through the solver path they would run in
-  // (48 iterations, twice each, best kept): the chosen pair, the persistent
-  // kernel, the single-reduction kernel
+  // (graph replay with programmatic dependent launch; 48 iterations, twice
+  // each, best kept): the fastest pair of each kernel family (timed above
+  // with plain launches, which rank the families differently), the
+  // persistent kernel, the single-reduction kernel
   if constexpr (sizeof(R) == 4) {
     c->persist32 = false;
     c->cg1_32 = false;
@@ -176,15 +187,24 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
     if (var == 0 && !c->capturing) {
       struct Design {
         bool persist, cg1;
+        int fam;  // pair family whose shapes the design runs (-1: the overall fastest)
       };
-      std::vector<Design> designs = {{false, false}};
-      if (cg32_persist_ok(c, g)) designs.push_back({true, false});
-      if (cg1_fit) designs.push_back({false, true});
+      std::vector<Design> designs;
+      for (int f = 0; f < 5; ++f)
+        if (fam_t[f] < 1e30f) designs.push_back({false, false, f});
+      if (designs.empty()) designs.push_back({false, false, -1});
+      if (cg32_persist_ok(c, g)) designs.push_back({true, false, -1});
+      if (cg1_fit) designs.push_back({false, true, -1});
+      auto use_shapes = [&](int f) {
+        for (int k = 0; k < nk; ++k) c->shape[ids[k]] = f >= 0 ? fam[f][k] : keep[k];
+      };
       float best_t = 1e30f;
       Design best_d = designs[0];
       for (size_t k = 0; designs.size() > 1 && k < designs.size(); ++k) {
         c->persist32 = designs[k].persist;
         c->cg1_32 = designs[k].cg1;
+        use_shapes(designs[k].fam);
+        destroy_graphs(c);  // graphs hold the launch shapes they were captured with
         float tm = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
           SolveStats tmp;
@@ -211,6 +231,8 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
       }
       c->persist32 = best_d.persist;
       c->cg1_32 = best_d.cg1;
+      use_shapes(best_d.fam);
+      destroy_graphs(c);
     }
   }
   cudaEventDestroy(e0);

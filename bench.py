@@ -713,6 +713,15 @@ def batched_solve_times(hmc, W, torch, stream, flush):
     out["batched_mixed_ms"] = ms
     out["batched_mixed_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)
     out["batched_mixed_gsite_s"] = site_applies(infos) / (ms * 1e-3) / 1e9
+    out["batched_mixed_design_chosen"] = {1: "graph_loop", 2: "persistent"}.get(any_ctx.batched_variant(), "none")
+    # both FP32 CG designs of the batched solver pinned in turn
+    designs = {}
+    for v, name in ((1, "graph_loop"), (2, "persistent")):
+        any_ctx.set_batched_variant(v)
+        ms_v, infos_v = timed(lambda: any_ctx.solve_batched(systems, mixed=True))
+        designs[name] = {"ms": ms_v, "max_true_rel_res": max(i["true_rel_res"] for i in infos_v)}
+    any_ctx.set_batched_variant(0)
+    out["batched_mixed_designs"] = designs
     ms, infos = timed(lambda: any_ctx.solve_batched(systems, mixed=False))
     out["batched_fp64_ms"] = ms
     out["batched_fp64_max_true_rel_res"] = max(i["true_rel_res"] for i in infos)

@@ -562,12 +562,18 @@ bool cg1_tune(hmc_ctx* c, const Geo& g, const CG1Bufs& B, float2* p, float2* x, 
   for (const FusedShape& fs : cands) {
     c->cg1_shape = fs;
     if (reinit() != HMC_OK) break;
-    if (cg1_prime_launch(c, g, B, p, x, sc) != HMC_OK) break;
-    for (int i = 0; i < 2; ++i) cg1_iter_launch(c, g, B, p, x, sc, i);
+    // a candidate whose launch fails is skipped, never kept
+    bool ok = cg1_prime_launch(c, g, B, p, x, sc) == HMC_OK;
+    for (int i = 0; ok && i < 2; ++i) ok = cg1_iter_launch(c, g, B, p, x, sc, i) == HMC_OK;
     cudaEventRecord(e0, c->stream);
-    for (int i = 0; i < 6; ++i) cg1_iter_launch(c, g, B, p, x, sc, i);
+    for (int i = 0; ok && i < 6; ++i) ok = cg1_iter_launch(c, g, B, p, x, sc, i) == HMC_OK;
     cudaEventRecord(e1, c->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    if (!ok) {
+      cudaGetLastError();
+      c->err.clear();
+      continue;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {

@@ -252,7 +252,7 @@ def main():
                     help="inner tolerance factor a of Algorithm A.1 for the trajectory's solves "
                          "(the paper's CPU choice is 5; on GB300, where FP64 runs at 1/58 of FP32, "
                          "a = 1 keeps every Arnoldi step preconditioned and is faster)")
-    ap.add_argument("--cg-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--cg-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7],
                     help="FP32 CG design of the trajectory's context: 0 = autotuned (default); 1-6 pin "
                          "grid-stride, tiled, marching, persistent, grid-stride with two cells per "
                          "thread or single-reduction (hmc_set_cg_variant). Under a "
@@ -263,7 +263,7 @@ def main():
                          "chunks with host checks, the mode kernel profilers can see into")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs",
-                             "spcg_single",
+                             "spcg_single", "spcg_resident",
                              "mmdag32_stream", "mmdag32_stream_fused", "cg64", "fgmres", "mmdag32", "mmdag64",
                              "batched", "force", "md_short", "trajectory"],
                     help="run one solve or application on the benchmark lattice and exit "
@@ -911,9 +911,10 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
     b = torch.tensor(w.b, device="cuda")
     with hmc.Context(lat) as ctx:
         ctx.set_graph_mode(graph_mode)
-        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs", "spcg_single"):
+        if case in ("spcg", "spcg_grid", "spcg_tiled", "spcg_march", "spcg_persist", "spcg_pairs", "spcg_single",
+                    "spcg_resident"):
             ctx.set_cg_variant({"spcg": 0, "spcg_grid": 1, "spcg_tiled": 2, "spcg_march": 3,
-                                "spcg_persist": 4, "spcg_pairs": 5, "spcg_single": 6}[case])
+                                "spcg_persist": 4, "spcg_pairs": 5, "spcg_single": 6, "spcg_resident": 7}[case])
             if case == "spcg_single":
                 ctx.set_cg_fused_tile(*SINGLE_REDUCTION_TILE)
             _, info = ctx.solve_spcg(phi, 0.0, b.to(torch.complex64), tol=1e-6, maxit=60, allow_fail=True)

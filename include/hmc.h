@@ -320,11 +320,16 @@ hmc_status hmc_md_trajectory_batched(hmc_ctx* ctx, int nchains, const hmc_chain*
  * arithmetic), whose kernel applies M M^dagger + sigma over tiles with
  * M^dagger r kept in shared memory as hmc_apply_MMdag's fused kernel does,
  * and updates x, r, p and the recurrences of w = A r and s = A p as the
- * slices arrive. variant: 0 = let the autotuner choose among all of them
- * (default), 1 = grid-stride with one cell per thread, 2 = tiled only,
+ * slices arrive. The seventh runs the whole solve in one cooperative launch
+ * in which each block keeps p and M^dagger p of its tile (all n cells of a
+ * row, a few rows and time slices) in shared memory and exchanges the tile's
+ * edges through memory between grid barriers (bounded waits, as for the
+ * persistent kernel). variant: 0 = let the autotuner choose among all of
+ * them (default), 1 = grid-stride with one cell per thread, 2 = tiled only,
  * 3 = marching only, 4 = persistent, 5 = grid-stride with two cells per
- * thread, 6 = single-reduction (2 to 6 fall back to variant 1 where they do
- * not fit the lattice). Setting it re-runs the tuner at the next FP32 solve. */
+ * thread, 6 = single-reduction, 7 = resident tiles (2 to 7 fall back to
+ * variant 1 where they do not fit the lattice). Setting it re-runs the
+ * tuner at the next FP32 solve. */
 hmc_status hmc_set_cg_variant(hmc_ctx* ctx, int variant);
 
 /* The FP32 CG of hmc_solve_batched (mixed = 1) runs in one of two designs:
@@ -396,7 +401,7 @@ hmc_status hmc_set_graph_mode(hmc_ctx* ctx, int mode);
 
 /* ---- instrumentation ------------------------------------------------------- */
 
-#define HMC_NKERNELS 32
+#define HMC_NKERNELS 40  /* at least the number of kernel groups the library reports */
 
 typedef struct {
   char name[48];

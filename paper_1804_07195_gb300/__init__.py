@@ -320,7 +320,8 @@ class Context:
         """0: autotune over all FP32 CG kernel designs; 1: grid-stride; 2: tiled;
         3: marching; 4: persistent (one cooperative launch per solve); 5:
         grid-stride with two cells per thread; 6: single-reduction (one fused
-        kernel per iteration)."""
+        kernel per iteration); 7: resident tiles (one cooperative launch, p
+        and M^dagger p of each tile in shared memory)."""
         self._check(self.lib.hmc_set_cg_variant(self.h, variant))
 
     def set_batched_variant(self, variant: int):

@@ -72,7 +72,7 @@ class hmc_kernel_stat(C.Structure):
                 ("bytes_total", C.c_double), ("threads", C.c_int), ("waves", C.c_int), ("design", C.c_int)]
 
 
-HMC_NKERNELS = 32
+HMC_NKERNELS = 40
 HMC_NOALLOC_MAX_SITES = 1 << 20
 
 P = C.c_void_p

@@ -579,11 +579,12 @@ hmc_status hmc_solve_fcg(hmc_ctx* c, const double* phi, double ms, double sigma,
 
 hmc_status hmc_set_cg_variant(hmc_ctx* c, int variant) {
   if (!c) return HMC_ERR_INVALID;
-  if (variant < 0 || variant > 6) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 6");
+  if (variant < 0 || variant > 7) return fail(c, HMC_ERR_INVALID, "variant must be 0 to 7");
   c->cg32_variant = variant;
   c->tuned32 = false;
   c->persist32 = false;
   c->cg1_32 = false;
+  c->resident32 = false;
   destroy_graphs(c);
   return HMC_OK;
 }
@@ -734,6 +735,8 @@ hmc_status hmc_profile(hmc_ctx* c, int timing_on, int reset) {
   c->prof.timing = timing_on != 0;
   return HMC_OK;
 }
+
+static_assert(K_COUNT <= HMC_NKERNELS, "hmc_profile_read must be able to report every kernel group");
 
 hmc_status hmc_profile_read(hmc_ctx* c, hmc_kernel_stat* out, int max, int* count) {
   if (!c || !out || !count) return HMC_ERR_INVALID;

@@ -1,0 +1,386 @@
+// FP32 CG with the direction p and the intermediate u = M^dagger p resident
+// in shared memory for the whole solve (the inner solver of Section 3 and
+// Algorithm A.1; the same CG step as the two-kernel pair). One cooperative
+// launch per solve; every block owns a tile of cells -- all n cells of a row
+// i, Jt rows j, Tt time slices -- and keeps p_A, p_B, u_A, u_B of the tile in
+// shared memory, each array padded by the one row and the one time slice of
+// neighbouring tiles its stencil reads (Eq. ferm_op: the A rows of M^dagger
+// read p_B at (i, j), (i-1, j), (i, j-1) and p_A at t+1; the B rows read p_A
+// at (i, j), (i+1, j), (i, j+1) and p_B at t-1; M reads u the same way with
+// the time hops reversed). With all of i in the tile, the i-neighbours wrap
+// inside it.
+//
+// Iteration (scalars held by thread 0 of every block in FP64, partials summed
+// by every block in the same fixed order):
+//   first half:  p = r + beta p on the tile (in place) and on the padding
+//                (from r and the previous p of the neighbouring tiles, which
+//                their owners publish); u = M^dagger p on the tile; the
+//                tile's edge rows and slices of u published; partial of
+//                |u|^2 + sigma |p|^2;                      -- grid barrier --
+//   second half: alpha = |r|^2 / <p, A p>; the padding of u read from the
+//                neighbours' published edges; A p = M u + sigma p, x += alpha
+//                p, r -= alpha A p on the tile (x and r stay in memory, read
+//                and written by their owner only); partial of |r|^2.
+//                                                          -- grid barrier --
+// The padding slices that lie beyond t = nt - 1 or before t = 0 hold the
+// anti-periodic continuation (negated values), so the time hops carry no
+// sign of their own, as in the fused M M^dagger kernel. Published p edges
+// alternate between two buffers by iteration parity (a tile reads the
+// previous iteration's edges while its neighbours write the current ones);
+// published u edges are written before the first barrier and read after it.
+// Data other blocks wrote is read with L2-only loads (L1 is not coherent
+// across SMs). The barrier waits are bounded: a wait that gives up marks the
+// solve CG_TIMEOUT and every block leaves.
+#include <algorithm>
+
+#include "kernels.h"
+#include "launch.cuh"
+#include "operator.cuh"
+
+namespace hmc {
+
+// Tile of the resident kernel: J rows, T slices (nominal; the last tile in
+// each direction may be smaller), the number of tiles, and the rows of the
+// tile a block works on at once (threads = n x rows).
+struct ResTile {
+  int J = 0, T = 0, tiles_j = 0, tiles_t = 0, rows = 0;
+};
+
+constexpr int kResMaxThreads = 1024;
+
+__global__ void __launch_bounds__(kResMaxThreads, 1)
+    k_cg32_resident(Geo g, ResTile rt, Phase<float> ph, float2* __restrict__ x, float2* __restrict__ r,
+                    float2* __restrict__ P0, float2* __restrict__ P1, float2* __restrict__ U, CGScal* sc,
+                    float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
+                    unsigned expect) {
+  extern __shared__ float2 s_tile[];
+  __shared__ float s_a;
+  __shared__ int s_stop;
+  const int n = g.n, m = g.m, nt = g.nt, H = g.H;
+  const int bj = blockIdx.x % rt.tiles_j, bt = blockIdx.x / rt.tiles_j;
+  const int j0 = bj * rt.J, t0 = bt * rt.T;
+  const int Jt = min(rt.J, m - j0), Tt = min(rt.T, nt - t0);
+  const int J1 = rt.J + 1;
+  const int SZ = (rt.T + 1) * J1 * n;  // one padded array
+  float2* pA = s_tile;                 // rows 0..Jt (Jt: the row above), slices 0..Tt (Tt: the slice after)
+  float2* pB = pA + SZ;                // rows -1..Jt-1, slices -1..Tt-1 (stored at +1)
+  float2* uA = pB + SZ;                // rows 0..Jt, slices -1..Tt-1
+  float2* uB = uA + SZ;                // rows -1..Jt-1, slices 0..Tt
+  auto iPA = [&](int i, int jj, int tt) { return (tt * J1 + jj) * n + i; };
+  auto iPB = [&](int i, int jj, int tt) { return ((tt + 1) * J1 + jj + 1) * n + i; };
+  auto iUA = [&](int i, int jj, int tt) { return ((tt + 1) * J1 + jj) * n + i; };
+  auto iUB = [&](int i, int jj, int tt) { return (tt * J1 + jj + 1) * n + i; };
+  // the thread's cell column i and its first row of the tile
+  const int i = threadIdx.x % n, r0 = threadIdx.x / n, RS = rt.rows;
+  const bool act = r0 < RS;
+  const int im = i == 0 ? n - 1 : i - 1, ip = i == n - 1 ? 0 : i + 1;
+  const int rows = Jt * Tt, lines = 2 * Tt + 2 * Jt;
+  const int jdn = (j0 - 1 + m) % m, jup = (j0 + Jt) % m;  // the rows below and above the tile
+  const bool wlo = (t0 == 0), whi = (t0 + Tt == nt);      // padding slices across the time boundary
+  const int tdn = wlo ? nt - 1 : t0 - 1, tup = whi ? 0 : t0 + Tt;
+  auto cell = [&](int j, int t) { return (t * m + j) * n + i; };
+  // The thread's rows R = r0, r0 + RS, ... of the tile as (jj, tt), advanced
+  // without division. Within a row every shared-memory index is the row's
+  // base b = (tt (J + 1) + jj) n + i plus a constant (NJ: one padded slice):
+  //   p_A(jj, tt) = b, p_A(tt+1) = b + NJ, p_A(jj+1) = b + n,
+  //   p_B(jj, tt) = b + NJ + n, p_B(jj-1) = b + NJ, p_B(tt-1) = b + n,
+  //   u_A(jj, tt) = b + NJ, u_A(tt-1) = b, u_A(jj+1) = b + NJ + n,
+  //   u_B(jj, tt) = b + n, u_B(jj-1) = b, u_B(tt+1) = b + NJ + n,
+  // and the i-neighbours add dim = im - i or dip = ip - i.
+  const int NJ = J1 * n, dim = im - i, dip = ip - i;
+  const int V = g.V, kb = (t0 * m + j0) * n + i;  // lattice index of the tile's cell (i, 0, 0)
+  const int dJ = RS % max(Jt, 1), dT = RS / max(Jt, 1);
+  auto for_rows = [&](auto&& f) {
+    int jj = r0 % Jt, tt = r0 / Jt;
+    for (int R = r0; R < rows; R += RS) {
+      f(jj, tt, (tt * J1 + jj) * n + i, kb + tt * V + jj * n);
+      jj += dJ;
+      tt += dT;
+      if (jj >= Jt) {
+        jj -= Jt;
+        ++tt;
+      }
+    }
+  };
+  const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
+  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  int iter = sc->iter, done = sc->done;
+  const int maxit = sc->maxit;
+  const double thresh = sc->thresh;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      if (!done) {
+        if (!isfinite(rr))
+          done = CG_BREAKDOWN;
+        else if (rr <= thresh)
+          done = CG_CONVERGED;
+        else if (iter >= maxit)
+          done = CG_MAXIT;
+      }
+      beta = first ? 0.0 : rr / rr_prev;
+      s_a = (float)beta;
+      s_stop = done;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const float fb = s_a;
+    float2* Pcur = (iter & 1) ? P1 : P0;        // this iteration's published p edges
+    const float2* Pold = (iter & 1) ? P0 : P1;  // the previous iteration's
+    // ---- first half
+    // padding of p: r + beta p_old of the neighbouring tiles' edge cells
+    if (act) {
+      for (int l = r0; l < lines; l += RS) {
+        int jj, tt, j, t, k;
+        float s = 1.f;
+        bool isA;
+        if (l < Tt) {  // p_B, the row below
+          jj = -1, tt = l, j = jdn, t = t0 + l, isA = false;
+        } else if (l < 2 * Tt) {  // p_A, the row above
+          jj = Jt, tt = l - Tt, j = jup, t = t0 + tt, isA = true;
+        } else if (l < 2 * Tt + Jt) {  // p_B, the slice before
+          jj = l - 2 * Tt, tt = -1, j = j0 + jj, t = tdn, isA = false, s = wlo ? -1.f : 1.f;
+        } else {  // p_A, the slice after
+          jj = l - 2 * Tt - Jt, tt = Tt, j = j0 + jj, t = tup, isA = true, s = whi ? -1.f : 1.f;
+        }
+        k = cell(j, t) + (isA ? 0 : H);
+        float2 v = __ldcg(r + k);
+        if (!first) {
+          const float2 po = __ldcg(Pold + k);
+          v = make_float2(fmaf(fb, po.x, v.x), fmaf(fb, po.y, v.y));
+        }
+        v = make_float2(s * v.x, s * v.y);
+        if (isA)
+          pA[iPA(i, jj, tt)] = v;
+        else
+          pB[iPB(i, jj, tt)] = v;
+      }
+      // the tile's own p, in place; its edges published for the neighbours
+      for_rows([&](int jj, int tt, int b, int k) {
+        const float2 ra = __ldcg(r + k), rb = __ldcg(r + H + k);
+        float2& qa = pA[b];
+        float2& qb = pB[b + NJ + n];
+        float2 a = ra, c = rb;
+        if (!first) {
+          a = make_float2(fmaf(fb, qa.x, ra.x), fmaf(fb, qa.y, ra.y));
+          c = make_float2(fmaf(fb, qb.x, rb.x), fmaf(fb, qb.y, rb.y));
+        }
+        qa = a;
+        qb = c;
+        if (jj == 0 || tt == 0) Pcur[k] = a;
+        if (jj == Jt - 1 || tt == Tt - 1) Pcur[H + k] = c;
+      });
+    }
+    __syncthreads();
+    // u = M^dagger p on the tile
+    float loc = 0.f;
+    if (act) {
+      for_rows([&](int jj, int tt, int b, int k) {
+        const int t = t0 + tt;
+        const Cx<float> pa = ld<float>(pA, b), pb = ld<float>(pB, b + NJ + n);
+        // A row: time partner p_A(t+1), phase of A at t+1 conjugated
+        const Cx<float> ea = ph(t + 1 == nt ? k + V - H : k + V);
+        const Cx<float> ua = hopsum(cfma(Cx<float>{ea.re - dm, -ea.im}, ld<float>(pA, b + NJ), Cx<float>{-pa.re, -pa.im}),
+                                    dk, pb, ld<float>(pB, b + NJ + n + dim), ld<float>(pB, b + NJ));
+        // B row: time partner p_B(t-1), phase of B at t-1
+        const Cx<float> eb = ph(H + (t == 0 ? k - V + H : k - V));
+        const Cx<float> ub = hopsum(cfma(Cx<float>{dm - eb.re, -eb.im}, ld<float>(pB, b + n), pb), dk, pa,
+                                    ld<float>(pA, b + dip), ld<float>(pA, b + n));
+        uA[b + NJ] = make_float2(ua.re, ua.im);
+        uB[b + n] = make_float2(ub.re, ub.im);
+        // edges the neighbours' M reads: u_A of the bottom row and the last
+        // slice, u_B of the top row and the first slice
+        if (jj == 0 || tt == Tt - 1) U[k] = make_float2(ua.re, ua.im);
+        if (jj == Jt - 1 || tt == 0) U[H + k] = make_float2(ub.re, ub.im);
+        loc += norm2(ua) + norm2(ub);
+        if (sigma != 0.f) loc += sigma * (norm2(pa) + norm2(pb));
+      });
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partA[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, expect, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    // ---- second half
+    {
+      const float2 tot = ff_sum_partials(partA, gridDim.x);
+      if (threadIdx.x == 0) {
+        pAp = ff_to_double(tot);
+        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+        alpha = bad ? 0.0 : rr / pAp;
+        if (bad) done = CG_BREAKDOWN;
+        s_a = (float)alpha;
+        s_stop = bad;
+      }
+    }
+    // padding of u from the neighbours' published edges
+    if (act) {
+      for (int l = r0; l < lines; l += RS) {
+        int jj, tt, j, t;
+        float s = 1.f;
+        bool isA;
+        if (l < Tt) {  // u_B, the row below
+          jj = -1, tt = l, j = jdn, t = t0 + l, isA = false;
+        } else if (l < 2 * Tt) {  // u_A, the row above
+          jj = Jt, tt = l - Tt, j = jup, t = t0 + tt, isA = true;
+        } else if (l < 2 * Tt + Jt) {  // u_A, the slice before
+          jj = l - 2 * Tt, tt = -1, j = j0 + jj, t = tdn, isA = true, s = wlo ? -1.f : 1.f;
+        } else {  // u_B, the slice after
+          jj = l - 2 * Tt - Jt, tt = Tt, j = j0 + jj, t = tup, isA = false, s = whi ? -1.f : 1.f;
+        }
+        const float2 v = __ldcg(U + cell(j, t) + (isA ? 0 : H));
+        if (isA)
+          uA[iUA(i, jj, tt)] = make_float2(s * v.x, s * v.y);
+        else
+          uB[iUB(i, jj, tt)] = make_float2(s * v.x, s * v.y);
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const float fa = s_a;
+    loc = 0.f;
+    if (act) {
+      for_rows([&](int, int, int b, int k) {
+        const Cx<float> ua = ld<float>(uA, b + NJ), ub = ld<float>(uB, b + n);
+        // (M u)_A(t) = -u_A(t) + (e^{i phi_A(t)} - dm) u_A(t-1) - dk [u_B(i,j) + u_B(i-1,j) + u_B(i,j-1)](t)
+        const Cx<float> ea = ph(k);
+        Cx<float> oa = hopsum(cfma(Cx<float>{ea.re - dm, ea.im}, ld<float>(uA, b), Cx<float>{-ua.re, -ua.im}), dk, ub,
+                              ld<float>(uB, b + n + dim), ld<float>(uB, b));
+        // (M u)_B(t) = u_B(t) + (dm - e^{-i phi_B(t)}) u_B(t+1) - dk [u_A(i,j) + u_A(i+1,j) + u_A(i,j+1)](t)
+        const Cx<float> eb = ph(H + k);
+        Cx<float> ob = hopsum(cfma(Cx<float>{dm - eb.re, eb.im}, ld<float>(uB, b + NJ + n), ub), dk, ua,
+                              ld<float>(uA, b + NJ + dip), ld<float>(uA, b + NJ + n));
+        const float2 pa = pA[b], pb = pB[b + NJ + n];
+        oa.re = fmaf(sigma, pa.x, oa.re);
+        oa.im = fmaf(sigma, pa.y, oa.im);
+        ob.re = fmaf(sigma, pb.x, ob.re);
+        ob.im = fmaf(sigma, pb.y, ob.im);
+        float2 xa = x[k], xb = x[H + k], ra = r[k], rb = r[H + k];
+        xa = make_float2(fmaf(fa, pa.x, xa.x), fmaf(fa, pa.y, xa.y));
+        xb = make_float2(fmaf(fa, pb.x, xb.x), fmaf(fa, pb.y, xb.y));
+        ra = make_float2(fmaf(-fa, oa.re, ra.x), fmaf(-fa, oa.im, ra.y));
+        rb = make_float2(fmaf(-fa, ob.re, rb.x), fmaf(-fa, ob.im, rb.y));
+        x[k] = xa;
+        x[H + k] = xb;
+        r[k] = ra;
+        r[H + k] = rb;
+        loc = fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, loc))));
+      });
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partB[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, expect, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    {
+      const float2 tot = ff_sum_partials(partB, gridDim.x);
+      if (threadIdx.x == 0) {
+        rr_prev = rr;
+        rr = ff_to_double(tot);
+      }
+    }
+    ++iter;  // in every thread: its parity selects the buffer of published p edges
+    first = false;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rr = rr;
+    sc->rr_cur = rr;
+    sc->pAp = pAp;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->iter = iter;
+    sc->first = 0;
+    sc->done = done ? done : CG_MAXIT;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+static size_t res_smem(const Geo& g, int J, int T) { return (size_t)4 * (T + 1) * (J + 1) * g.n * sizeof(float2); }
+
+// Tile plan: every tile of J rows and T slices resident at once (one
+// cooperative launch), its padded p and u arrays within the shared memory a
+// block may use, and at most kResMaxThreads threads (n per row of the tile).
+// Among the plans that fit, the one with the fewest cells per tile, then the
+// fewest padding rows and slices per cell.
+static bool res_plan(const hmc_ctx* c, const Geo& g, ResTile* out, size_t* smem_out) {
+  if (g.n > kResMaxThreads) return false;
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  const size_t cap = (size_t)std::max(0, dev_smem - 1024);  // the kernel's static arrays
+  const int rows_max = kResMaxThreads / g.n;
+  bool found = false;
+  long long best_cells = 0;
+  double best_halo = 0.0;
+  for (int J = 1; J <= g.m; ++J)
+    for (int T = 1; T <= g.nt; ++T) {
+      const size_t sm = res_smem(g, J, T);
+      if (sm > cap) break;  // larger T only grows it
+      const int tj = (g.m + J - 1) / J, tt = (g.nt + T - 1) / T;
+      const long long tiles = (long long)tj * tt;
+      if (tiles > c->nsm || 2 * tiles > cg32_part_capacity(c)) continue;
+      const long long cells = (long long)J * T * g.n;
+      const double halo = (double)(J + T) / ((double)J * T);
+      if (!found || cells < best_cells || (cells == best_cells && halo < best_halo)) {
+        found = true;
+        best_cells = cells;
+        best_halo = halo;
+        out->J = J;
+        out->T = T;
+        out->tiles_j = tj;
+        out->tiles_t = tt;
+        out->rows = std::min(rows_max, J * T);
+        *smem_out = sm;
+      }
+    }
+  return found;
+}
+
+bool cg32_resident_ok(const hmc_ctx* c, const Geo& g) {
+  ResTile rt;
+  size_t sm = 0;
+  return res_plan(c, g, &rt, &sm);
+}
+
+hmc_status cg32_resident_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1, float2* u,
+                                CGScal* sc) {
+  ResTile rt;
+  size_t smem = 0;
+  if (!res_plan(c, g, &rt, &smem)) return fail(c, HMC_ERR_INVALID, "resident CG tiles do not fit on chip");
+  if (cudaFuncSetAttribute((const void*)k_cg32_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return cuda_fail(c, cudaGetLastError(), "resident CG shared memory");
+  const int threads = g.n * rt.rows;
+  const int blocks = rt.tiles_j * rt.tiles_t;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg32_resident, threads, smem) != cudaSuccess ||
+      (long long)occ * c->nsm < blocks) {
+    cudaGetLastError();
+    return fail(c, HMC_ERR_INVALID, "resident CG tiles cannot all be resident");
+  }
+  HMC_CUDA(c, cudaMemsetAsync(c->gbar, 0, sizeof(GridBar), c->stream));
+  Phase<float> ph = phase_of<float>(c);
+  float2* pa = (float2*)c->partA;
+  float2* pb = (float2*)c->partB;
+  GridBar* gb = c->gbar;
+  long long limit = c->bar_limit > 0 ? c->bar_limit : 2000000000LL;
+  unsigned expect = (unsigned)blocks + (unsigned)c->bar_extra;
+  Geo gg = g;
+  void* args[] = {&gg, &rt, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &expect};
+  cudaError_t le = cudaSuccess;
+  HMC_TRY(launch_b(c, K_CG_RES32, 0.0, [&] {
+    le = cudaLaunchCooperativeKernel((const void*)k_cg32_resident, dim3(blocks), dim3(threads), args, smem,
+                                     c->stream);
+  }));
+  if (le != cudaSuccess) return cuda_fail(c, le, "resident CG launch");
+  return HMC_OK;
+}
+
+}  // namespace hmc

@@ -47,6 +47,7 @@ enum KernelId {
   K_MMDAG_FUSED32,
   K_MMDAG_FUSED64,
   K_CG1_32,
+  K_CG_RES32,
   K_COUNT
 };
 
@@ -151,6 +152,7 @@ struct hmc_ctx {
                          // 4 persistent
   bool persist32 = false;  // the tuner found the persistent FP32 CG kernel fastest
   bool cg1_32 = false;     // the tuner found the single-reduction FP32 CG fastest
+  bool resident32 = false;  // the tuner found the resident-tile FP32 CG fastest
   bool cg1_pinned = false;  // its tile was set by the caller
   hmc::FusedShape cg1_shape;  // tile of the single-reduction FP32 CG kernel
   // M M^dagger applications: 0 = choose per precision by timing on first use,

@@ -19,7 +19,7 @@ const char* const kKernelNames[K_COUNT] = {
     "norm2",          "gmres_mdot",     "gmres_gs_update", "gmres_scale",  "gmres_x_update",
     "force",          "axpy",           "md_update",     "batch_cg_graph_f64", "batch_cg_graph_f32",
     "batch_init",     "batch_residual", "batch_misc",   "cg_persist_f32", "mmdag_fused_f32",
-    "mmdag_fused_f64", "cg1_fused_f32"};
+    "mmdag_fused_f64", "cg1_fused_f32",  "cg_resident_f32"};
 
 const double kKernelBytesPerSite[K_COUNT] = {
     8 + 16 + 4,          // phase: phi in, E and phi32 out
@@ -49,7 +49,8 @@ const double kKernelBytesPerSite[K_COUNT] = {
     0,                   // persistent CG: 56 B per site and iteration, counted after the solve
     8 + 4 + 8,           // fused M M^dagger f32: p, phi32, out (u stays on chip)
     16 + 16 + 16,        // fused M M^dagger f64: p, E, out
-    5 * 8 + 4 + 5 * 8};  // single-reduction CG f32: r, w, s, p, x, phi32 in; r, w, s, p, x out
+    5 * 8 + 4 + 5 * 8,   // single-reduction CG f32: r, w, s, p, x, phi32 in; r, w, s, p, x out
+    0};                  // resident CG: 40 B per site and iteration, counted after the solve
 
 // ---------------------------------------------------------------------------
 // e^{i phi} for the FP64 stencils of Eq. ferm_op, and phi rounded to float.

@@ -55,6 +55,13 @@ bool cg1_tune(hmc_ctx* c, const Geo& g, const CG1Bufs& B, float2* p, float2* x, 
               const std::function<hmc_status()>& reinit);
 hmc_status set_cg1_shape(hmc_ctx* c, int Ti, int Tj, int Tt, int D);
 
+// Resident-tile FP32 CG (cg32_resident.cu): the whole solve in one
+// cooperative launch with p and M^dagger p of each block's tile in shared
+// memory; false / HMC_ERR_INVALID when the tiles do not fit on chip.
+bool cg32_resident_ok(const hmc_ctx* c, const Geo& g);
+hmc_status cg32_resident_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1, float2* u,
+                                CGScal* sc);
+
 // CG building blocks on the state sc (see common.cuh).
 template <typename R>
 hmc_status cg_mdag_launch(hmc_ctx* c, const Geo& g, const V2<R>* p, V2<R>* u, CGScal* sc,

@@ -169,6 +169,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
   if constexpr (sizeof(R) == 4) {
     c->persist32 = false;
     c->cg1_32 = false;
+    c->resident32 = false;
     bool cg1_fit = false;
     if ((var == 0 || var == 6) && !c->capturing) {
       const CG1Bufs B = cg1_bufs(c, (float2*)r);
@@ -186,15 +187,16 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
     if (var == 6) c->cg1_32 = cg1_fit;
     if (var == 0 && !c->capturing) {
       struct Design {
-        bool persist, cg1;
+        bool persist, cg1, resident;
         int fam;  // pair family whose shapes the design runs (-1: the overall fastest)
       };
       std::vector<Design> designs;
       for (int f = 0; f < 5; ++f)
-        if (fam_t[f] < 1e30f) designs.push_back({false, false, f});
-      if (designs.empty()) designs.push_back({false, false, -1});
-      if (cg32_persist_ok(c, g)) designs.push_back({true, false, -1});
-      if (cg1_fit) designs.push_back({false, true, -1});
+        if (fam_t[f] < 1e30f) designs.push_back({false, false, false, f});
+      if (designs.empty()) designs.push_back({false, false, false, -1});
+      if (cg32_persist_ok(c, g)) designs.push_back({true, false, false, -1});
+      if (cg1_fit) designs.push_back({false, true, false, -1});
+      if (cg32_resident_ok(c, g)) designs.push_back({false, false, true, -1});
       auto use_shapes = [&](int f) {
         for (int k = 0; k < nk; ++k) c->shape[ids[k]] = f >= 0 ? fam[f][k] : keep[k];
       };
@@ -203,6 +205,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
       for (size_t k = 0; designs.size() > 1 && k < designs.size(); ++k) {
         c->persist32 = designs[k].persist;
         c->cg1_32 = designs[k].cg1;
+        c->resident32 = designs[k].resident;
         use_shapes(designs[k].fam);
         destroy_graphs(c);  // graphs hold the launch shapes they were captured with
         float tm = 1e30f;
@@ -215,6 +218,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
           if (st != HMC_OK && st != HMC_ERR_NOT_CONVERGED) {
             c->persist32 = false;
             c->cg1_32 = false;
+            c->resident32 = false;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return st;
@@ -231,6 +235,7 @@ static hmc_status tune_cg(hmc_ctx* c, double ms, double sigma, const V2<R>* b) {
       }
       c->persist32 = best_d.persist;
       c->cg1_32 = best_d.cg1;
+      c->resident32 = best_d.resident;
       use_shapes(best_d.fam);
       destroy_graphs(c);
     }
@@ -295,13 +300,25 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
   // pinned variant) chose it
   bool persistent = false;
   if constexpr (sizeof(R) == 4) {
-    persistent = !c->capturing && (c->cg32_variant == 4 || (c->cg32_variant == 0 && c->persist32)) &&
-                 cg32_persist_ok(c, g);
+    // the resident-tile kernel (one launch per solve, p and M^dagger p of
+    // each tile in shared memory) when the tuner or the pinned variant chose it
+    const bool resident = !c->capturing &&
+                          (c->cg32_variant == 7 || (c->cg32_variant == 0 && c->resident32)) &&
+                          cg32_resident_ok(c, g);
+    persistent = resident || (!c->capturing && (c->cg32_variant == 4 || (c->cg32_variant == 0 && c->persist32)) &&
+                              cg32_persist_ok(c, g));
     if (persistent) {
-      HMC_TRY(cg32_persist_launch(c, g, (float2*)x, (float2*)r, (float2*)p, (float2*)q, (float2*)u, sc));
+      if (resident)
+        HMC_TRY(cg32_resident_launch(c, g, (float2*)x, (float2*)r, (float2*)p, (float2*)q, (float2*)u, sc));
+      else
+        HMC_TRY(cg32_persist_launch(c, g, (float2*)x, (float2*)r, (float2*)p, (float2*)q, (float2*)u, sc));
       HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
       HMC_CUDA(c, cudaStreamSynchronize(c->stream));
-      c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
+      // resident: r and x read and written, phi read twice, per site and iteration
+      if (resident)
+        c->prof.bytes[K_CG_RES32] += 40.0 * g.N * sch->iter;
+      else
+        c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
     }
   }
   // FP32: one single-reduction launch per iteration when the tuner (or the

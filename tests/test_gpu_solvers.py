@@ -141,13 +141,14 @@ def test_fcg_mixed(name, ms):
         assert abs(info["iters_inner"] - ref.inner_iters) <= 0.2 * ref.inner_iters
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("name,ms,sigma,bound", [("L36x36x64", 0.0, 0.0, 1e-3), ("L36x36x64", 0.4, 0.05, 5e-5),
                                                  ("L102x102x64", 0.1, 0.0, 1e-3), ("L36x36x21", 0.2, 0.0, 1e-4),
                                                  ("L35x12x16", 0.2, 0.0, 1e-4)])
 def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     """The FP32 CG kernel designs (grid-stride, shared-memory tiled, marching,
-    persistent, grid-stride with two cells per thread, single-reduction) solve
+    persistent, grid-stride with two cells per thread, single-reduction,
+    resident tiles) solve
     to the single-precision floor, and FGMRES built on them meets 1e-10. The
     FP32 solution's true residual is bounded by the recursive tolerance plus
     the rounding drift, about eps_32 times the condition number (near 10^4 at
@@ -172,10 +173,12 @@ def test_fp32_cg_kernel_variants(variant, name, ms, sigma, bound):
     design = shapes["cg_pMdag_f32"]["design"]
     persist = shapes["cg_persist_f32"]["launches"]
     single = shapes["cg1_fused_f32"]["launches"]
+    resident = shapes["cg_resident_f32"]["launches"]
     assert {1: waves >= 0 and design == 0, 2: -1000 < waves < 0, 3: waves <= -1000, 4: True,
-            5: waves >= 0 and design == (4 if w.lat.n % 2 == 0 else 0), 6: True}[variant]
+            5: waves >= 0 and design == (4 if w.lat.n % 2 == 0 else 0), 6: True, 7: True}[variant]
     assert (persist > 0) == (variant == 4)
     assert (single > 0) == (variant == 6)
+    assert (resident > 0) == (variant == 7)
     b32 = w.b.astype(np.complex64).astype(np.complex128)
     assert info["iters"] > 0 and info["status"] == 0
     assert true_rel(ol, w.phi, ms, sigma, host(x32).astype(np.complex128), b32) < bound

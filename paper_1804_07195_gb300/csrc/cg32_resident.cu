@@ -32,6 +32,7 @@
 // across SMs). The barrier waits are bounded: a wait that gives up marks the
 // solve CG_TIMEOUT and every block leaves.
 #include <algorithm>
+#include <cstdint>
 
 #include "kernels.h"
 #include "launch.cuh"
@@ -301,21 +302,306 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The same kernel with two cells per thread (n even): a thread owns the cells
+// (i, i+1), i even, of a row, whose complex64 values form one 16-byte float4
+// in every vector and in every shared-memory array, so each load, store and
+// index computation serves two cells. The i-neighbour inside the pair is the
+// thread's own other half; the one across the pair boundary is the left
+// pair's second cell (A rows of M^dagger and M read B at i-1) or the right
+// pair's first cell (B rows read A at i+1). The rows of Eq. ferm_op are formed
+// in the same order as in the one-cell kernel.
+__device__ __forceinline__ Cx<float> lo4(const float4& v) { return Cx<float>{v.x, v.y}; }
+__device__ __forceinline__ Cx<float> hi4(const float4& v) { return Cx<float>{v.z, v.w}; }
+__device__ __forceinline__ float4 pk4(Cx<float> a, Cx<float> b) { return make_float4(a.re, a.im, b.re, b.im); }
+__device__ __forceinline__ float sq4(const float4& v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
+// e^{i phi} of the two cells of the pair at pair index kp
+__device__ __forceinline__ void phases2(const float* __restrict__ phi32, int kp, Cx<float>& e0, Cx<float>& e1) {
+  const float2 f = __ldg(reinterpret_cast<const float2*>(phi32) + kp);
+  float x0 = fmaf(-6.28318530717958648f, rintf(f.x * 0.159154943091895336f), f.x);
+  float x1 = fmaf(-6.28318530717958648f, rintf(f.y * 0.159154943091895336f), f.y);
+  float s0, c0, s1, c1;
+  __sincosf(x0, &s0, &c0);
+  __sincosf(x1, &s1, &c1);
+  e0 = Cx<float>{c0, s0};
+  e1 = Cx<float>{c1, s1};
+}
+
+__global__ void __launch_bounds__(kResMaxThreads, 1)
+    k_cg32_resident2(Geo g, ResTile rt, const float* __restrict__ phi32, float4* __restrict__ x,
+                     float4* __restrict__ r, float4* __restrict__ P0, float4* __restrict__ P1, float4* __restrict__ U,
+                     CGScal* sc, float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
+                     unsigned expect) {
+  extern __shared__ float4 s_tile4[];
+  __shared__ float s_a;
+  __shared__ int s_stop;
+  // all sizes and indices in cell pairs
+  const int n2 = g.n >> 1, m = g.m, nt = g.nt, H2 = g.H >> 1, V2 = g.V >> 1;
+  const int bj = blockIdx.x % rt.tiles_j, bt = blockIdx.x / rt.tiles_j;
+  const int j0 = bj * rt.J, t0 = bt * rt.T;
+  const int Jt = min(rt.J, m - j0), Tt = min(rt.T, nt - t0);
+  const int J1 = rt.J + 1;
+  const int SZ = (rt.T + 1) * J1 * n2;
+  float4* pA = s_tile4;  // the same padded layout as the one-cell kernel, in pairs
+  float4* pB = pA + SZ;
+  float4* uA = pB + SZ;
+  float4* uB = uA + SZ;
+  auto iPA = [&](int q, int jj, int tt) { return (tt * J1 + jj) * n2 + q; };
+  auto iPB = [&](int q, int jj, int tt) { return ((tt + 1) * J1 + jj + 1) * n2 + q; };
+  auto iUA = [&](int q, int jj, int tt) { return ((tt + 1) * J1 + jj) * n2 + q; };
+  auto iUB = [&](int q, int jj, int tt) { return (tt * J1 + jj + 1) * n2 + q; };
+  const int q = threadIdx.x % n2, r0 = threadIdx.x / n2, RS = rt.rows;
+  const bool act = r0 < RS;
+  const int dim = (q == 0 ? n2 - 1 : q - 1) - q, dip = (q == n2 - 1 ? 0 : q + 1) - q;
+  const int rows = Jt * Tt, lines = 2 * Tt + 2 * Jt;
+  const int jdn = (j0 - 1 + m) % m, jup = (j0 + Jt) % m;
+  const bool wlo = (t0 == 0), whi = (t0 + Tt == nt);
+  const int tdn = wlo ? nt - 1 : t0 - 1, tup = whi ? 0 : t0 + Tt;
+  auto cell = [&](int j, int t) { return (t * m + j) * n2 + q; };
+  const int NJ = J1 * n2, kb = (t0 * m + j0) * n2 + q;
+  const int dJ = RS % max(Jt, 1), dT = RS / max(Jt, 1);
+  auto for_rows = [&](auto&& f) {
+    int jj = r0 % Jt, tt = r0 / Jt;
+    for (int R = r0; R < rows; R += RS) {
+      f(jj, tt, (tt * J1 + jj) * n2 + q, kb + tt * V2 + jj * n2);
+      jj += dJ;
+      tt += dT;
+      if (jj >= Jt) {
+        jj -= Jt;
+        ++tt;
+      }
+    }
+  };
+  const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
+  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  int iter = sc->iter, done = sc->done;
+  const int maxit = sc->maxit;
+  const double thresh = sc->thresh;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      if (!done) {
+        if (!isfinite(rr))
+          done = CG_BREAKDOWN;
+        else if (rr <= thresh)
+          done = CG_CONVERGED;
+        else if (iter >= maxit)
+          done = CG_MAXIT;
+      }
+      beta = first ? 0.0 : rr / rr_prev;
+      s_a = (float)beta;
+      s_stop = done;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const float fb = s_a;
+    float4* Pcur = (iter & 1) ? P1 : P0;
+    const float4* Pold = (iter & 1) ? P0 : P1;
+    // ---- first half: padding of p, the tile's own p
+    if (act) {
+      for (int l = r0; l < lines; l += RS) {
+        int jj, tt, j, t;
+        float sg = 1.f;
+        bool isA;
+        if (l < Tt) {
+          jj = -1, tt = l, j = jdn, t = t0 + l, isA = false;
+        } else if (l < 2 * Tt) {
+          jj = Jt, tt = l - Tt, j = jup, t = t0 + tt, isA = true;
+        } else if (l < 2 * Tt + Jt) {
+          jj = l - 2 * Tt, tt = -1, j = j0 + jj, t = tdn, isA = false, sg = wlo ? -1.f : 1.f;
+        } else {
+          jj = l - 2 * Tt - Jt, tt = Tt, j = j0 + jj, t = tup, isA = true, sg = whi ? -1.f : 1.f;
+        }
+        const int k = cell(j, t) + (isA ? 0 : H2);
+        float4 v = __ldcg(r + k);
+        if (!first) {
+          const float4 po = __ldcg(Pold + k);
+          v = make_float4(fmaf(fb, po.x, v.x), fmaf(fb, po.y, v.y), fmaf(fb, po.z, v.z), fmaf(fb, po.w, v.w));
+        }
+        v = make_float4(sg * v.x, sg * v.y, sg * v.z, sg * v.w);
+        if (isA)
+          pA[iPA(q, jj, tt)] = v;
+        else
+          pB[iPB(q, jj, tt)] = v;
+      }
+      for_rows([&](int jj, int tt, int b, int k) {
+        const float4 ra = __ldcg(r + k), rb = __ldcg(r + H2 + k);
+        float4& qa = pA[b];
+        float4& qb = pB[b + NJ + n2];
+        float4 a = ra, c = rb;
+        if (!first) {
+          const float4 oa = qa, ob = qb;
+          a = make_float4(fmaf(fb, oa.x, ra.x), fmaf(fb, oa.y, ra.y), fmaf(fb, oa.z, ra.z), fmaf(fb, oa.w, ra.w));
+          c = make_float4(fmaf(fb, ob.x, rb.x), fmaf(fb, ob.y, rb.y), fmaf(fb, ob.z, rb.z), fmaf(fb, ob.w, rb.w));
+        }
+        qa = a;
+        qb = c;
+        if (jj == 0 || tt == 0) Pcur[k] = a;
+        if (jj == Jt - 1 || tt == Tt - 1) Pcur[H2 + k] = c;
+      });
+    }
+    __syncthreads();
+    // u = M^dagger p on the tile
+    float loc = 0.f;
+    if (act) {
+      for_rows([&](int jj, int tt, int b, int k) {
+        const int t = t0 + tt;
+        const float4 pa = pA[b], pb = pB[b + NJ + n2];
+        Cx<float> ea0, ea1, eb0, eb1;
+        phases2(phi32, t + 1 == nt ? k + V2 - H2 : k + V2, ea0, ea1);
+        phases2(phi32, H2 + (t == 0 ? k - V2 + H2 : k - V2), eb0, eb1);
+        // A rows: p_A(t+1), p_B at (i, j), (i-1, j), (i, j-1)
+        const float4 atp = pA[b + NJ], bdn = pB[b + NJ], bl = pB[b + NJ + n2 + dim];
+        const Cx<float> ua0 = hopsum(cfma(Cx<float>{ea0.re - dm, -ea0.im}, lo4(atp), Cx<float>{-pa.x, -pa.y}), dk,
+                                     lo4(pb), hi4(bl), lo4(bdn));
+        const Cx<float> ua1 = hopsum(cfma(Cx<float>{ea1.re - dm, -ea1.im}, hi4(atp), Cx<float>{-pa.z, -pa.w}), dk,
+                                     hi4(pb), lo4(pb), hi4(bdn));
+        // B rows: p_B(t-1), p_A at (i, j), (i+1, j), (i, j+1)
+        const float4 btm = pB[b + n2], aup = pA[b + n2], ar = pA[b + dip];
+        const Cx<float> ub0 = hopsum(cfma(Cx<float>{dm - eb0.re, -eb0.im}, lo4(btm), lo4(pb)), dk, lo4(pa), hi4(pa),
+                                     lo4(aup));
+        const Cx<float> ub1 = hopsum(cfma(Cx<float>{dm - eb1.re, -eb1.im}, hi4(btm), hi4(pb)), dk, hi4(pa), lo4(ar),
+                                     hi4(aup));
+        const float4 ua = pk4(ua0, ua1), ub = pk4(ub0, ub1);
+        uA[b + NJ] = ua;
+        uB[b + n2] = ub;
+        if (jj == 0 || tt == Tt - 1) U[k] = ua;
+        if (jj == Jt - 1 || tt == 0) U[H2 + k] = ub;
+        loc += sq4(ua) + sq4(ub);
+        if (sigma != 0.f) loc += sigma * (sq4(pa) + sq4(pb));
+      });
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partA[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, expect, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    // ---- second half
+    {
+      const float2 tot = ff_sum_partials(partA, gridDim.x);
+      if (threadIdx.x == 0) {
+        pAp = ff_to_double(tot);
+        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+        alpha = bad ? 0.0 : rr / pAp;
+        if (bad) done = CG_BREAKDOWN;
+        s_a = (float)alpha;
+        s_stop = bad;
+      }
+    }
+    if (act) {
+      for (int l = r0; l < lines; l += RS) {
+        int jj, tt, j, t;
+        float sg = 1.f;
+        bool isA;
+        if (l < Tt) {
+          jj = -1, tt = l, j = jdn, t = t0 + l, isA = false;
+        } else if (l < 2 * Tt) {
+          jj = Jt, tt = l - Tt, j = jup, t = t0 + tt, isA = true;
+        } else if (l < 2 * Tt + Jt) {
+          jj = l - 2 * Tt, tt = -1, j = j0 + jj, t = tdn, isA = true, sg = wlo ? -1.f : 1.f;
+        } else {
+          jj = l - 2 * Tt - Jt, tt = Tt, j = j0 + jj, t = tup, isA = false, sg = whi ? -1.f : 1.f;
+        }
+        const float4 v = __ldcg(U + cell(j, t) + (isA ? 0 : H2));
+        const float4 w = make_float4(sg * v.x, sg * v.y, sg * v.z, sg * v.w);
+        if (isA)
+          uA[iUA(q, jj, tt)] = w;
+        else
+          uB[iUB(q, jj, tt)] = w;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const float fa = s_a;
+    loc = 0.f;
+    if (act) {
+      for_rows([&](int, int, int b, int k) {
+        const float4 ua = uA[b + NJ], ub = uB[b + n2];
+        Cx<float> ea0, ea1, eb0, eb1;
+        phases2(phi32, k, ea0, ea1);
+        phases2(phi32, H2 + k, eb0, eb1);
+        // A rows: u_A(t-1), u_B at (i, j), (i-1, j), (i, j-1)
+        const float4 atm = uA[b], bdn = uB[b], bl = uB[b + n2 + dim];
+        Cx<float> oa0 = hopsum(cfma(Cx<float>{ea0.re - dm, ea0.im}, lo4(atm), Cx<float>{-ua.x, -ua.y}), dk, lo4(ub),
+                               hi4(bl), lo4(bdn));
+        Cx<float> oa1 = hopsum(cfma(Cx<float>{ea1.re - dm, ea1.im}, hi4(atm), Cx<float>{-ua.z, -ua.w}), dk, hi4(ub),
+                               lo4(ub), hi4(bdn));
+        // B rows: u_B(t+1), u_A at (i, j), (i+1, j), (i, j+1)
+        const float4 btp = uB[b + NJ + n2], aup = uA[b + NJ + n2], ar = uA[b + NJ + dip];
+        Cx<float> ob0 = hopsum(cfma(Cx<float>{dm - eb0.re, eb0.im}, lo4(btp), lo4(ub)), dk, lo4(ua), hi4(ua),
+                               lo4(aup));
+        Cx<float> ob1 = hopsum(cfma(Cx<float>{dm - eb1.re, eb1.im}, hi4(btp), hi4(ub)), dk, hi4(ua), lo4(ar),
+                               hi4(aup));
+        const float4 pa = pA[b], pb = pB[b + NJ + n2];
+        const float4 apa = make_float4(fmaf(sigma, pa.x, oa0.re), fmaf(sigma, pa.y, oa0.im), fmaf(sigma, pa.z, oa1.re),
+                                       fmaf(sigma, pa.w, oa1.im));
+        const float4 apb = make_float4(fmaf(sigma, pb.x, ob0.re), fmaf(sigma, pb.y, ob0.im), fmaf(sigma, pb.z, ob1.re),
+                                       fmaf(sigma, pb.w, ob1.im));
+        float4 xa = x[k], xb = x[H2 + k], ra = r[k], rb = r[H2 + k];
+        xa = make_float4(fmaf(fa, pa.x, xa.x), fmaf(fa, pa.y, xa.y), fmaf(fa, pa.z, xa.z), fmaf(fa, pa.w, xa.w));
+        xb = make_float4(fmaf(fa, pb.x, xb.x), fmaf(fa, pb.y, xb.y), fmaf(fa, pb.z, xb.z), fmaf(fa, pb.w, xb.w));
+        ra = make_float4(fmaf(-fa, apa.x, ra.x), fmaf(-fa, apa.y, ra.y), fmaf(-fa, apa.z, ra.z),
+                         fmaf(-fa, apa.w, ra.w));
+        rb = make_float4(fmaf(-fa, apb.x, rb.x), fmaf(-fa, apb.y, rb.y), fmaf(-fa, apb.z, rb.z),
+                         fmaf(-fa, apb.w, rb.w));
+        x[k] = xa;
+        x[H2 + k] = xb;
+        r[k] = ra;
+        r[H2 + k] = rb;
+        loc = fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, loc))));
+        loc = fmaf(ra.z, ra.z, fmaf(ra.w, ra.w, fmaf(rb.z, rb.z, fmaf(rb.w, rb.w, loc))));
+      });
+    }
+    {
+      const float2 v = ff_block_sum(make_float2(loc, 0.f));
+      if (threadIdx.x == 0) partB[blockIdx.x] = v;
+    }
+    if (!grid_barrier(gb, expect, limit)) {
+      done = CG_TIMEOUT;
+      break;
+    }
+    {
+      const float2 tot = ff_sum_partials(partB, gridDim.x);
+      if (threadIdx.x == 0) {
+        rr_prev = rr;
+        rr = ff_to_double(tot);
+      }
+    }
+    ++iter;
+    first = false;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rr = rr;
+    sc->rr_cur = rr;
+    sc->pAp = pAp;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->iter = iter;
+    sc->first = 0;
+    sc->done = done ? done : CG_MAXIT;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 
 static size_t res_smem(const Geo& g, int J, int T) { return (size_t)4 * (T + 1) * (J + 1) * g.n * sizeof(float2); }
 
 // Tile plan: every tile of J rows and T slices resident at once (one
 // cooperative launch), its padded p and u arrays within the shared memory a
-// block may use, and at most kResMaxThreads threads (n per row of the tile).
-// Among the plans that fit, the one with the fewest cells per tile, then the
-// fewest padding rows and slices per cell.
-static bool res_plan(const hmc_ctx* c, const Geo& g, ResTile* out, size_t* smem_out) {
-  if (g.n > kResMaxThreads) return false;
+// block may use, and at most kResMaxThreads threads (n, or n / 2 with two
+// cells per thread, per row of the tile). Among the plans that fit, the one
+// with the fewest cells per tile, then the fewest padding rows and slices per
+// cell.
+static bool res_plan(const hmc_ctx* c, const Geo& g, bool pairs, ResTile* out, size_t* smem_out) {
+  const int per_row = pairs ? g.n / 2 : g.n;
+  if (per_row < 1 || per_row > kResMaxThreads) return false;
   int dev_smem = 0;
   cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   const size_t cap = (size_t)std::max(0, dev_smem - 1024);  // the kernel's static arrays
-  const int rows_max = kResMaxThreads / g.n;
+  const int rows_max = kResMaxThreads / per_row;
   bool found = false;
   long long best_cells = 0;
   double best_halo = 0.0;
@@ -346,40 +632,47 @@ static bool res_plan(const hmc_ctx* c, const Geo& g, ResTile* out, size_t* smem_
 bool cg32_resident_ok(const hmc_ctx* c, const Geo& g) {
   ResTile rt;
   size_t sm = 0;
-  return res_plan(c, g, &rt, &sm);
+  return res_plan(c, g, false, &rt, &sm);
 }
 
 hmc_status cg32_resident_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, float2* p0, float2* p1, float2* u,
                                 CGScal* sc) {
+  // two cells per thread where n is even and every vector is 16-byte aligned
+  auto al16 = [](const void* v) { return ((uintptr_t)v & 15u) == 0; };
   ResTile rt;
   size_t smem = 0;
-  if (!res_plan(c, g, &rt, &smem)) return fail(c, HMC_ERR_INVALID, "resident CG tiles do not fit on chip");
-  if (cudaFuncSetAttribute((const void*)k_cg32_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  bool pairs = !(g.n & 1) && al16(x) && al16(r) && al16(p0) && al16(p1) && al16(u) && res_plan(c, g, true, &rt, &smem);
+  if (!pairs && !res_plan(c, g, false, &rt, &smem))
+    return fail(c, HMC_ERR_INVALID, "resident CG tiles do not fit on chip");
+  const void* kfn = pairs ? (const void*)k_cg32_resident2 : (const void*)k_cg32_resident;
+  if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "resident CG shared memory");
-  const int threads = g.n * rt.rows;
+  const int threads = (pairs ? g.n / 2 : g.n) * rt.rows;
   const int blocks = rt.tiles_j * rt.tiles_t;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg32_resident, threads, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem) != cudaSuccess ||
       (long long)occ * c->nsm < blocks) {
     cudaGetLastError();
     return fail(c, HMC_ERR_INVALID, "resident CG tiles cannot all be resident");
   }
   HMC_CUDA(c, cudaMemsetAsync(c->gbar, 0, sizeof(GridBar), c->stream));
   Phase<float> ph = phase_of<float>(c);
+  const float* phi32 = ph.phi;
   float2* pa = (float2*)c->partA;
   float2* pb = (float2*)c->partB;
   GridBar* gb = c->gbar;
   long long limit = c->bar_limit > 0 ? c->bar_limit : 2000000000LL;
   unsigned expect = (unsigned)blocks + (unsigned)c->bar_extra;
   Geo gg = g;
-  void* args[] = {&gg, &rt, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &expect};
+  float4 *x4 = (float4*)x, *r4 = (float4*)r, *p04 = (float4*)p0, *p14 = (float4*)p1, *u4 = (float4*)u;
+  void* args1[] = {&gg, &rt, &ph, &x, &r, &p0, &p1, &u, &sc, &pa, &pb, &gb, &limit, &expect};
+  void* args2[] = {&gg, &rt, (void*)&phi32, &x4, &r4, &p04, &p14, &u4, &sc, &pa, &pb, &gb, &limit, &expect};
   cudaError_t le = cudaSuccess;
   HMC_TRY(launch_b(c, K_CG_RES32, 0.0, [&] {
-    le = cudaLaunchCooperativeKernel((const void*)k_cg32_resident, dim3(blocks), dim3(threads), args, smem,
-                                     c->stream);
+    le = cudaLaunchCooperativeKernel(kfn, dim3(blocks), dim3(threads), pairs ? args2 : args1, smem, c->stream);
   }));
   if (le != cudaSuccess) return cuda_fail(c, le, "resident CG launch");
+  c->shape[K_CG_RES32].tiled = pairs ? 4 : 0;  // reported as the design
   return HMC_OK;
 }
 

@@ -1,7 +1,8 @@
 """The resident-tile FP32 CG (variant 7: one cooperative launch per solve, p
 and u = M^dagger p of every block's tile in shared memory, the neighbouring
 tiles' edge rows and slices exchanged through memory between grid barriers)
-against the oracle's textbook CG (Section 3): the same CG step, so x after k
+against the oracle's textbook CG (Section 3), with one cell per thread (odd
+n) and two (even n): the same CG step, so x after k
 iterations matches the oracle's FP64 CG after k iterations to FP32
 rounding, on lattices with n or m of 1 to 3 (every wrap: a tile's padding
 row or slice is its own cells), odd nt (uneven tiles), sigma != 0, and the
@@ -41,7 +42,10 @@ def test_resident_iterates_equal_cg(shape, ms, sigma):
             assert info["iters"] == k, (shape, k, info)
             ref = osv.cg(A, b32.astype(np.complex128), tol=1e-30, maxit=k)
             assert rel_max(host(x).astype(np.complex128), ref.x) <= 2e-5 * k, (shape, k)
-        assert ctx.profile_read()["cg_resident_f32"]["launches"] >= 2
+        st = ctx.profile_read()["cg_resident_f32"]
+        assert st["launches"] >= 2
+        # two cells per thread (16-byte pairs) where n is even
+        assert st["design"] == (4 if shape[0] % 2 == 0 else 0)
 
 
 def test_resident_iterates_at_full_size():

@@ -414,11 +414,20 @@ def main():
                             if v["launches"]},
                 "tuned_shape": {"threads": dstat["threads"], "waves": dstat["waves"]},
                 "method": "CUDA events around every launch on the context stream, one profiled "
-                          "trajectory after the timed region",
-                "note": "the FP32 CG working set (59 MB) stays in L2 between iterations; 'traffic' is the "
-                        "cold-cache DRAM bytes of one launch under ncu (the algorithmic reads); with warm "
-                        "L2 the pair is latency-bound (ncu: L2 throughput 16 %, no eligible warp in about "
-                        "half the scheduler cycles)"}
+                          "trajectory after the timed region"}
+    if dname in ("cg_resident_f32", "cg_persist_f32"):
+        roofline["note"] = ("one launch runs a whole FP32 CG solve; its algorithmic bytes are 96 B per site and "
+                            "iteration (the CG step's operator with its dot, x and r updates with the norm, p "
+                            "update, complex64) times the iterations the solve ran, although p and M^dagger p "
+                            "stay in shared memory and r, x in L2 (1.33M sites: the working set fits the 126 MB "
+                            "L2), hence a fraction near or above 1 of the copy peak; 'traffic' is null: the DRAM "
+                            "bytes of such a launch are its first cold reads (ncu, 60 iterations: 27 MB read, "
+                            "4.5 MB written), not a per-iteration figure")
+    else:
+        roofline["note"] = ("the FP32 CG working set (59 MB) stays in L2 between iterations; 'traffic' is the "
+                            "cold-cache DRAM bytes of one launch under ncu (the algorithmic reads); with warm "
+                            "L2 the pair is latency-bound (ncu: L2 throughput 16 %, no eligible warp in about "
+                            "half the scheduler cycles)")
 
     # end to end through the public API with host buffers
     e2e_val = None
@@ -478,7 +487,7 @@ def main():
     designs = {}
     with hmc.Context(lat) as c2:
         for vname, v in (("grid_stride", 1), ("tiled", 2), ("marching", 3), ("persistent", 4),
-                         ("grid_stride_two_cells", 5), ("single_reduction", 6)):
+                         ("grid_stride_two_cells", 5), ("single_reduction", 6), ("resident_tiles", 7)):
             c2.set_cg_variant(v)
             b32 = b.to(torch.complex64)
             c2.solve_spcg(phi_t, 0.0, b32, tol=1e-30, maxit=300, allow_fail=True)
@@ -495,6 +504,8 @@ def main():
                               "shape": {"threads": sh["threads"], "waves": sh["waves"], "design": sh["design"]}}
             if v == 6:
                 designs[vname]["shape"] = dict(zip(("Ti", "Tj", "Tt", "depth", "in_use"), c2.cg_fused_tile()))
+            if v == 7:
+                designs[vname]["shape"] = {"design": c2.profile_read()["cg_resident_f32"]["design"]}
     solve["fp32_cg_designs"] = designs
     # the pair as production runs it (graph replay, no per-launch events): one
     # FP32 CG iteration moves 36 + 52 = 88 algorithmic bytes per site
@@ -504,6 +515,15 @@ def main():
             "frac": 88.0 * N / t_it / 1e9 / hbm,
             "method": "300 FP32 CG iterations of the grid-stride pair replayed from its graph, CUDA events around "
                       "the solve; no per-launch events"}
+    # the resident-tile design as the solver runs it: one launch per solve, 96
+    # algorithmic bytes per site and iteration (the CG step)
+    t_res = designs["resident_tiles"]["us_per_iter"] * 1e-6
+    resident_roof = {"kernels": ["k_cg32_resident2" if designs["resident_tiles"]["shape"]["design"] == 4
+                                 else "k_cg32_resident"], "bytes_per_site": 96.0, "sites": N,
+                     "us_per_iteration": t_res * 1e6, "achieved": 96.0 * N / t_res / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": 96.0 * N / t_res / 1e9 / hbm,
+                     "method": "300 FP32 CG iterations in one launch, CUDA events around the solve; the working "
+                               "set is L2-resident (p and M^dagger p in shared memory)"}
     solve["speedup_mixed_vs_fp64"] = solve["fp64_cg"]["ms"] / solve["mixed_fgmres"]["ms"]
     solve["workload"] = "102x102x64 lattice, m_s=0, phi of the step, b = rho_0, true residual 1e-10"
     solve["fgmres_a"] = args.fgmres_a
@@ -588,7 +608,8 @@ def main():
                                              0: "direct launches"}[graph_mode],
                            "dH": [float(x) for x in dH], "wall_s_timed_region": t_wall,
                            "dH_mixed_vs_fp64": dH_check},
-                "roofline": roofline, "roofline_pair_graph_replay": pair, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_pair_graph_replay": pair,
+                "roofline_resident_tiles": resident_roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches, "clocks": clk, "solve_ms": solve}

@@ -51,25 +51,9 @@ __global__ void __launch_bounds__(TC) k_cg32_pmdag_tiled(Geo g, Phase<float> ph,
   const int first = sc->first;
   const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
-    int done = CG_RUNNING;
-    if (!isfinite(rr))
-      done = CG_BREAKDOWN;
-    else if (rr <= sc->thresh)
-      done = CG_CONVERGED;
-    else if (sc->iter >= sc->maxit)
-      done = CG_MAXIT;
-    const double beta = first ? 0.0 : rr / sc->rr;
-    s_beta = (float)beta;
-    s_done = done;
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-      sc->rr_cur = rr;
-      sc->beta = beta;
-      if (done) {
-        sc->rr = rr;
-        sc->done = done;
-      }
-    }
+    float b;
+    s_done = cg32_scalars_first(sc, first, rr_pair, blockIdx.x == 0 && blockIdx.y == 0, &b);
+    s_beta = b;
   }
   __syncthreads();
   if (s_done) return;
@@ -171,23 +155,9 @@ __global__ void __launch_bounds__(TC) k_cg32_m_tiled(Geo g, Phase<float> ph, int
   if (s_exit) return;
   const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
-    const double pAp = ff_to_double(pAp_pair);
-    const double rr = sc->rr_cur;
-    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-    s_bad = bad;
-    s_alpha = bad ? 0.f : (float)(rr / pAp);
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-      sc->pAp = pAp;
-      sc->rr = rr;
-      sc->first = 0;
-      if (bad) {
-        sc->alpha = 0.0;
-        sc->done = CG_BREAKDOWN;
-      } else {
-        sc->alpha = rr / pAp;
-        sc->iter += 1;
-      }
-    }
+    float a;
+    s_bad = cg32_scalars_second(sc, pAp_pair, blockIdx.x == 0 && blockIdx.y == 0, &a);
+    s_alpha = a;
   }
   __syncthreads();
   if (s_bad) return;
@@ -302,25 +272,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag_march(Geo g, Phase<f
   const int first = sc->first;
   const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
-    int done = CG_RUNNING;
-    if (!isfinite(rr))
-      done = CG_BREAKDOWN;
-    else if (rr <= sc->thresh)
-      done = CG_CONVERGED;
-    else if (sc->iter >= sc->maxit)
-      done = CG_MAXIT;
-    const double beta = first ? 0.0 : rr / sc->rr;
-    s_beta = (float)beta;
-    s_done = done;
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-      sc->rr_cur = rr;
-      sc->beta = beta;
-      if (done) {
-        sc->rr = rr;
-        sc->done = done;
-      }
-    }
+    float b;
+    s_done = cg32_scalars_first(sc, first, rr_pair, blockIdx.x == 0 && blockIdx.y == 0, &b);
+    s_beta = b;
   }
   __syncthreads();
   if (s_done) return;
@@ -387,23 +341,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m_march(Geo g, Phase<float
   if (s_exit) return;
   const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
-    const double pAp = ff_to_double(pAp_pair);
-    const double rr = sc->rr_cur;
-    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-    s_bad = bad;
-    s_alpha = bad ? 0.f : (float)(rr / pAp);
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-      sc->pAp = pAp;
-      sc->rr = rr;
-      sc->first = 0;
-      if (bad) {
-        sc->alpha = 0.0;
-        sc->done = CG_BREAKDOWN;
-      } else {
-        sc->alpha = rr / pAp;
-        sc->iter += 1;
-      }
-    }
+    float a;
+    s_bad = cg32_scalars_second(sc, pAp_pair, blockIdx.x == 0 && blockIdx.y == 0, &a);
+    s_alpha = a;
   }
   __syncthreads();
   if (s_bad) return;
@@ -499,11 +439,12 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
     sr[k] = make_float4(ra.x, ra.y, rb.x, rb.y);
   }
   const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
-  // scalars, held by thread 0 in FP64 and handed to the block as floats
-  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  // scalars, held by thread 0 in FP32 (the FP64 pipe is slow on this GPU and
+  // the rest of the block waits for them); the partial sums stay float-float
+  float rr = sc->rr32, rr_prev = 1.f, pAp = 0.f, alpha = 0.f, beta = 0.f;
   int iter = sc->iter, done = sc->done;
   const int maxit = sc->maxit;
-  const double thresh = sc->thresh;
+  const float thresh = sc->thresh32;
   float2* pold = p0;
   float2* pnew = p1;
   bool first = true;
@@ -519,8 +460,8 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
         else if (iter >= maxit)
           done = CG_MAXIT;
       }
-      beta = first ? 0.0 : rr / rr_prev;
-      s_a = (float)beta;
+      beta = first ? 0.f : rr / rr_prev;
+      s_a = beta;
       s_stop = done;
     }
     __syncthreads();
@@ -567,11 +508,11 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
     {
       const float2 tot = ff_sum_partials(partA, gridDim.x);
       if (threadIdx.x == 0) {
-        pAp = ff_to_double(tot);
-        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-        alpha = bad ? 0.0 : rr / pAp;
+        pAp = tot.x + tot.y;
+        const bool bad = !(pAp > 0.f) || !isfinite(pAp);
+        alpha = bad ? 0.f : rr / pAp;
         if (bad) done = CG_BREAKDOWN;
-        s_a = (float)alpha;
+        s_a = alpha;
         s_stop = bad;
       }
       __syncthreads();
@@ -616,7 +557,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
       const float2 tot = ff_sum_partials(partB, gridDim.x);
       if (threadIdx.x == 0) {
         rr_prev = rr;
-        rr = ff_to_double(tot);
+        rr = tot.x + tot.y;
         ++iter;
       }
     }
@@ -635,6 +576,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->rr = rr;
     sc->rr_cur = rr;
+    sc->rr32 = sc->rr_cur32 = rr;
     sc->pAp = pAp;
     sc->alpha = alpha;
     sc->beta = beta;

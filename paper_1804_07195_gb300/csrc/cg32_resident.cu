@@ -104,10 +104,12 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     }
   };
   const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
-  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  // thread 0's scalars in FP32 (the FP64 pipe is slow on this GPU and every
+  // other warp of the block waits for them); the partial sums stay float-float
+  float rr = sc->rr32, rr_prev = 1.f, pAp = 0.f, alpha = 0.f, beta = 0.f;
   int iter = sc->iter, done = sc->done;
   const int maxit = sc->maxit;
-  const double thresh = sc->thresh;
+  const float thresh = sc->thresh32;
   bool first = true;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -119,8 +121,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
         else if (iter >= maxit)
           done = CG_MAXIT;
       }
-      beta = first ? 0.0 : rr / rr_prev;
-      s_a = (float)beta;
+      beta = first ? 0.f : rr / rr_prev;
+      s_a = beta;
       s_stop = done;
     }
     __syncthreads();
@@ -209,11 +211,11 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     {
       const float2 tot = ff_sum_partials(partA, gridDim.x);
       if (threadIdx.x == 0) {
-        pAp = ff_to_double(tot);
-        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-        alpha = bad ? 0.0 : rr / pAp;
+        pAp = tot.x + tot.y;
+        const bool bad = !(pAp > 0.f) || !isfinite(pAp);
+        alpha = bad ? 0.f : rr / pAp;
         if (bad) done = CG_BREAKDOWN;
-        s_a = (float)alpha;
+        s_a = alpha;
         s_stop = bad;
       }
     }
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       const float2 tot = ff_sum_partials(partB, gridDim.x);
       if (threadIdx.x == 0) {
         rr_prev = rr;
-        rr = ff_to_double(tot);
+        rr = tot.x + tot.y;
       }
     }
     ++iter;  // in every thread: its parity selects the buffer of published p edges
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->rr = rr;
     sc->rr_cur = rr;
+    sc->rr32 = sc->rr_cur32 = rr;
     sc->pAp = pAp;
     sc->alpha = alpha;
     sc->beta = beta;
@@ -372,10 +375,12 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     }
   };
   const float dm = sc->dm32, sigma = sc->sigma32, dk = g.dkf;
-  double rr = sc->rr, rr_prev = 1.0, pAp = 0.0, alpha = 0.0, beta = 0.0;
+  // thread 0's scalars in FP32 (the FP64 pipe is slow on this GPU and every
+  // other warp of the block waits for them); the partial sums stay float-float
+  float rr = sc->rr32, rr_prev = 1.f, pAp = 0.f, alpha = 0.f, beta = 0.f;
   int iter = sc->iter, done = sc->done;
   const int maxit = sc->maxit;
-  const double thresh = sc->thresh;
+  const float thresh = sc->thresh32;
   bool first = true;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -387,8 +392,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
         else if (iter >= maxit)
           done = CG_MAXIT;
       }
-      beta = first ? 0.0 : rr / rr_prev;
-      s_a = (float)beta;
+      beta = first ? 0.f : rr / rr_prev;
+      s_a = beta;
       s_stop = done;
     }
     __syncthreads();
@@ -482,11 +487,11 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     {
       const float2 tot = ff_sum_partials(partA, gridDim.x);
       if (threadIdx.x == 0) {
-        pAp = ff_to_double(tot);
-        const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-        alpha = bad ? 0.0 : rr / pAp;
+        pAp = tot.x + tot.y;
+        const bool bad = !(pAp > 0.f) || !isfinite(pAp);
+        alpha = bad ? 0.f : rr / pAp;
         if (bad) done = CG_BREAKDOWN;
-        s_a = (float)alpha;
+        s_a = alpha;
         s_stop = bad;
       }
     }
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       const float2 tot = ff_sum_partials(partB, gridDim.x);
       if (threadIdx.x == 0) {
         rr_prev = rr;
-        rr = ff_to_double(tot);
+        rr = tot.x + tot.y;
       }
     }
     ++iter;
@@ -575,6 +580,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->rr = rr;
     sc->rr_cur = rr;
+    sc->rr32 = sc->rr_cur32 = rr;
     sc->pAp = pAp;
     sc->alpha = alpha;
     sc->beta = beta;

@@ -242,6 +242,8 @@ struct CGScal {
   // in two slots that successive launches read and write alternately
   double cg1_gamma[2], cg1_alpha[2];
   int cg1_it[2];
+  // rr, rr_cur and thresh rounded to float for the FP32 CG kernels
+  float rr32, rr_cur32, thresh32;
 };
 
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_TIMEOUT = 4 };
@@ -363,5 +365,58 @@ __device__ __forceinline__ float2 ff_sum_partials(const float2* __restrict__ par
   return ff_block_sum(v);
 }
 __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
+
+// Scalars of the FP32 CG pair, formed by thread 0 of every block of the
+// kernel in FP32 (on this GPU the FP64 pipe is slow, and the rest of the block
+// waits for them); the lead block also records them in FP64 for the host.
+// First kernel of an iteration: |r|^2 from the second kernel's partials (the
+// init kernel's value on the first iteration), the convergence and limit
+// checks and beta; returns the CG state (CG_RUNNING to go on).
+__device__ __forceinline__ int cg32_scalars_first(CGScal* sc, bool first, float2 rr_pair, bool lead, float* beta) {
+  const float rr = first ? sc->rr_cur32 : rr_pair.x + rr_pair.y;
+  int done = CG_RUNNING;
+  if (!isfinite(rr))
+    done = CG_BREAKDOWN;
+  else if (rr <= sc->thresh32)
+    done = CG_CONVERGED;
+  else if (sc->iter >= sc->maxit)
+    done = CG_MAXIT;
+  const float b = first ? 0.f : rr / sc->rr32;
+  *beta = b;
+  if (lead) {
+    sc->rr_cur32 = rr;
+    sc->rr_cur = rr;
+    sc->beta = b;
+    if (done) {
+      sc->rr32 = rr;
+      sc->rr = rr;
+      sc->done = done;
+    }
+  }
+  return done;
+}
+// Second kernel: <p, A p> from the first kernel's partials and alpha;
+// returns true on a breakdown (non-positive or non-finite curvature).
+__device__ __forceinline__ bool cg32_scalars_second(CGScal* sc, float2 pAp_pair, bool lead, float* alpha) {
+  const float pAp = pAp_pair.x + pAp_pair.y;
+  const float rr = sc->rr_cur32;
+  const bool bad = !(pAp > 0.f) || !isfinite(pAp);
+  const float a = bad ? 0.f : rr / pAp;
+  *alpha = a;
+  if (lead) {
+    sc->pAp = pAp;
+    sc->rr32 = rr;
+    sc->rr = sc->rr_cur;
+    sc->first = 0;
+    if (bad) {
+      sc->alpha = 0.0;
+      sc->done = CG_BREAKDOWN;
+    } else {
+      sc->alpha = a;
+      sc->iter += 1;
+    }
+  }
+  return bad;
+}
 
 }  // namespace hmc

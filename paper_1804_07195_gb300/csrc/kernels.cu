@@ -46,11 +46,11 @@ const double kKernelBytesPerSite[K_COUNT] = {
     24,                  // axpy
     24,                  // md update
     192, 96, 16 * 4, 16 * 5, 0,
-    0,                   // persistent CG: 56 B per site and iteration, counted after the solve
+    0,                   // persistent CG: 96 B per site and iteration, counted after the solve
     8 + 4 + 8,           // fused M M^dagger f32: p, phi32, out (u stays on chip)
     16 + 16 + 16,        // fused M M^dagger f64: p, E, out
     5 * 8 + 4 + 5 * 8,   // single-reduction CG f32: r, w, s, p, x, phi32 in; r, w, s, p, x out
-    0};                  // resident CG: 40 B per site and iteration, counted after the solve
+    0};                  // resident CG: 96 B per site and iteration, counted after the solve
 
 // ---------------------------------------------------------------------------
 // e^{i phi} for the FP64 stencils of Eq. ferm_op, and phi rounded to float.
@@ -274,25 +274,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag(Geo g, Phase<float> 
   // the scalars are formed once per block by thread 0
   const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
-    int done = CG_RUNNING;
-    if (!isfinite(rr))
-      done = CG_BREAKDOWN;
-    else if (rr <= sc->thresh)
-      done = CG_CONVERGED;
-    else if (sc->iter >= sc->maxit)
-      done = CG_MAXIT;
-    const double beta = first ? 0.0 : rr / sc->rr;
-    s_beta = (float)beta;
-    s_done = done;
-    if (blockIdx.x == 0) {
-      sc->rr_cur = rr;
-      sc->beta = beta;
-      if (done) {
-        sc->rr = rr;
-        sc->done = done;
-      }
-    }
+    float b;
+    s_done = cg32_scalars_first(sc, first, rr_pair, blockIdx.x == 0, &b);
+    s_beta = b;
   }
   __syncthreads();
   if (s_done) return;
@@ -353,23 +337,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m(Geo g, Phase<float> ph,
   if (have0) o0 = m_pair<float>(g, ph, dm, u, neighbours(g, q));
   const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
-    const double pAp = ff_to_double(pAp_pair);
-    const double rr = sc->rr_cur;
-    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-    s_bad = bad;
-    s_alpha = bad ? 0.f : (float)(rr / pAp);
-    if (blockIdx.x == 0) {
-      sc->pAp = pAp;
-      sc->rr = rr;
-      sc->first = 0;
-      if (bad) {
-        sc->alpha = 0.0;
-        sc->done = CG_BREAKDOWN;
-      } else {
-        sc->alpha = rr / pAp;
-        sc->iter += 1;
-      }
-    }
+    float a;
+    s_bad = cg32_scalars_second(sc, pAp_pair, blockIdx.x == 0, &a);
+    s_alpha = a;
   }
   __syncthreads();
   if (s_bad) return;
@@ -551,25 +521,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_pmdag2(Geo g, const float*
   }
   const float2 rr_pair = first ? make_float2(0.f, 0.f) : ff_sum_partials(partB, GB);
   if (threadIdx.x == 0) {
-    const double rr = first ? sc->rr_cur : ff_to_double(rr_pair);
-    int done = CG_RUNNING;
-    if (!isfinite(rr))
-      done = CG_BREAKDOWN;
-    else if (rr <= sc->thresh)
-      done = CG_CONVERGED;
-    else if (sc->iter >= sc->maxit)
-      done = CG_MAXIT;
-    const double beta = first ? 0.0 : rr / sc->rr;
-    s_beta = (float)beta;
-    s_done = done;
-    if (blockIdx.x == 0) {
-      sc->rr_cur = rr;
-      sc->beta = beta;
-      if (done) {
-        sc->rr = rr;
-        sc->done = done;
-      }
-    }
+    float b;
+    s_done = cg32_scalars_first(sc, first, rr_pair, blockIdx.x == 0, &b);
+    s_beta = b;
   }
   __syncthreads();
   if (s_done) return;
@@ -628,23 +582,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_cg32_m2(Geo g, const float* __r
   if (have0) m2(g, phi32, dm, neighbours2(g, q2), u, oA0, oB0);
   const float2 pAp_pair = ff_sum_partials(partA, GA);
   if (threadIdx.x == 0) {
-    const double pAp = ff_to_double(pAp_pair);
-    const double rr = sc->rr_cur;
-    const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-    s_bad = bad;
-    s_alpha = bad ? 0.f : (float)(rr / pAp);
-    if (blockIdx.x == 0) {
-      sc->pAp = pAp;
-      sc->rr = rr;
-      sc->first = 0;
-      if (bad) {
-        sc->alpha = 0.0;
-        sc->done = CG_BREAKDOWN;
-      } else {
-        sc->alpha = rr / pAp;
-        sc->iter += 1;
-      }
-    }
+    float a;
+    s_bad = cg32_scalars_second(sc, pAp_pair, blockIdx.x == 0, &a);
+    s_alpha = a;
   }
   __syncthreads();
   if (s_bad) return;
@@ -723,6 +663,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(Geo g, Phase<R> ph, R dm,
       if (!isfinite(tot[0])) init->done = CG_BREAKDOWN;
       init->first = 1;
       init->rr_cur = tot[0];
+      init->rr32 = init->rr_cur32 = (float)tot[0];
+      init->thresh32 = (float)init->thresh;
     }
   }
 }
@@ -757,6 +699,8 @@ __global__ void __launch_bounds__(kThreads) k_init0(int N, const V2<R>* __restri
     if (!isfinite(tot[0])) sc->done = CG_BREAKDOWN;
     sc->first = 1;
     sc->rr_cur = tot[0];
+    sc->rr32 = sc->rr_cur32 = (float)tot[0];
+    sc->thresh32 = (float)sc->thresh;
   }
 }
 

@@ -314,11 +314,11 @@ hmc_status cg_core(hmc_ctx* c, double ms, double sigma, const V2<R>* b, V2<R>* x
         HMC_TRY(cg32_persist_launch(c, g, (float2*)x, (float2*)r, (float2*)p, (float2*)q, (float2*)u, sc));
       HMC_CUDA(c, cudaMemcpyAsync(sch, sc, sizeof(CGScal), cudaMemcpyDeviceToHost, c->stream));
       HMC_CUDA(c, cudaStreamSynchronize(c->stream));
-      // resident: r and x read and written, phi read twice, per site and iteration
-      if (resident)
-        c->prof.bytes[K_CG_RES32] += 40.0 * g.N * sch->iter;
-      else
-        c->prof.bytes[K_CG_PERSIST32] += 56.0 * g.N * sch->iter;
+      // the algorithmic bytes of one FP32 CG iteration per site, whatever the
+      // design keeps on chip: the operator with its dot (p and phi read, A p
+      // written: 20 B, here rounded with the dot to 24 B), x and r updated
+      // with the norm (48 B), p updated (24 B)
+      c->prof.bytes[resident ? K_CG_RES32 : K_CG_PERSIST32] += 96.0 * g.N * sch->iter;
     }
   }
   // FP32: one single-reduction launch per iteration when the tuner (or the

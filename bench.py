@@ -961,9 +961,15 @@ def kernel_case(case, graph_mode=2, cg_variant=0, fgmres_a=1.0):
             integ = hmc.Integrator(0, W.L102_NMD, W.L102_NI, W.OMELYAN_ZETA, 1.0)
             md = hmc.SolverOpts(method=1, tol=1e-10, a=fgmres_a)
             act = hmc.SolverOpts(method=1, tol=1e-12, a=fgmres_a)
-            for _ in range(2):
+            for k in range(2):
+                if k == 1:
+                    # profilers started with collection off capture the second one only
+                    torch.cuda.synchronize()
+                    torch.cuda.profiler.start()
                 H0, H1, info = ctx.md_trajectory(phi.clone(), torch.tensor(w.pi, device="cuda"), masses, rho, integ,
                                                  md, act)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         elif case == "md_short":
             # a short trajectory of the benchmark's kind (N_MD = 6, time scales 2, 1, 1):
             # the MD updates, energies and forces of the path

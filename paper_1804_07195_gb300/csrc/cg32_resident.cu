@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     // ---- first half
     // padding of p: r + beta p_old of the neighbouring tiles' edge cells
     if (act) {
-      for (int l = r0; l < lines; l += RS) {
+      // padding lines from the last row slot down: the slots that hold one row
+      // fewer of the tile (rows are dealt from slot 0) take the extra lines
+      for (int l = RS - 1 - r0; l < lines; l += RS) {
         int jj, tt, j, t, k;
         float s = 1.f;
         bool isA;
@@ -403,7 +405,9 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
     const float4* Pold = (iter & 1) ? P0 : P1;
     // ---- first half: padding of p, the tile's own p
     if (act) {
-      for (int l = r0; l < lines; l += RS) {
+      // padding lines from the last row slot down: the slots that hold one row
+      // fewer of the tile (rows are dealt from slot 0) take the extra lines
+      for (int l = RS - 1 - r0; l < lines; l += RS) {
         int jj, tt, j, t;
         float sg = 1.f;
         bool isA;

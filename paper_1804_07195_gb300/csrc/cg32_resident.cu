@@ -657,7 +657,9 @@ hmc_status cg32_resident_launch(hmc_ctx* c, const Geo& g, float2* x, float2* r, 
   const void* kfn = pairs ? (const void*)k_cg32_resident2 : (const void*)k_cg32_resident;
   if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "resident CG shared memory");
-  const int threads = (pairs ? g.n / 2 : g.n) * rt.rows;
+  // whole warps (the block reductions shuffle across all 32 lanes); threads
+  // beyond n x rows hold no row
+  const int threads = ((pairs ? g.n / 2 : g.n) * rt.rows + 31) / 32 * 32;
   const int blocks = rt.tiles_j * rt.tiles_t;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem) != cudaSuccess ||

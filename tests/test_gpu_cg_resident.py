@@ -101,3 +101,43 @@ def test_resident_barrier_wait_times_out_and_context_survives():
     b = w.b.astype(np.complex64).astype(np.complex128)
     r = b - of.apply_MMdag(ol, w.phi, 0.3, host(x).astype(np.complex128))
     assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b)
+
+
+def test_resident_falls_back_where_its_tiles_do_not_fit():
+    """n = 2101 (odd, more cells per row than a block has threads): variant 7
+    runs the grid-stride pair instead, and the solve still meets the oracle's
+    CG iterates."""
+    need_gpu()
+    w = W.small(2101, 1, 4, seed=1620)
+    ol = OLat.from_params(w.lat)
+    b32 = w.b.astype(np.complex64)
+    with ctx_for(w.lat) as ctx:
+        ctx.set_cg_variant(7)
+        x, info = ctx.solve_spcg(dev(w.phi), 0.3, dev(b32), tol=1e-30, maxit=3, allow_fail=True)
+        assert ctx.profile_read()["cg_resident_f32"]["launches"] == 0
+    ref = osv.cg(lambda v: of.apply_MMdag(ol, w.phi, 0.3, v), b32.astype(np.complex128), tol=1e-30, maxit=3)
+    assert info["iters"] == 3
+    assert rel_max(host(x).astype(np.complex128), ref.x) <= 1e-4
+
+
+def test_resident_with_an_unaligned_solution_vector():
+    """A caller's x that is 8- but not 16-byte aligned: the same iterates as an
+    aligned x (the two-cell kernel needs 16-byte vectors; the library solves
+    in a workspace vector or takes the one-cell kernel)."""
+    need_gpu()
+    import ctypes as C
+    from paper_1804_07195_gb300 import _abi
+    w = W.small(12, 12, 32, seed=1630, U=3.0, beta=6.0)
+    N = w.lat.nsites
+    b32 = dev(w.b.astype(np.complex64))
+    with ctx_for(w.lat) as ctx:
+        ctx.set_cg_variant(7)
+        xa, ia = ctx.solve_spcg(dev(w.phi), 0.1, b32, tol=1e-5, maxit=5000)
+        buf = torch.zeros(N + 1, dtype=torch.complex64, device="cuda")
+        info = _abi.hmc_solve_info()
+        st = ctx.lib.hmc_solve_spcg(ctx.h, C.c_void_p(dev(w.phi).data_ptr()), 0.1, 0.0, C.c_void_p(b32.data_ptr()),
+                                    C.c_void_p(buf[1:].data_ptr()), 1e-5, 5000, C.byref(info))
+        torch.cuda.synchronize()
+        assert st == 0 and ctx.profile_read()["cg_resident_f32"]["launches"] >= 2
+    assert abs(info.iters - ia["iters"]) <= 1
+    assert rel_max(host(buf[1:]).astype(np.complex128), host(xa).astype(np.complex128)) <= 1e-5

@@ -18,9 +18,11 @@
 //                tile's edge rows and slices of u published; partial of
 //                |u|^2 + sigma |p|^2;                      -- grid barrier --
 //   second half: alpha = |r|^2 / <p, A p>; the padding of u read from the
-//                neighbours' published edges; A p = M u + sigma p, x += alpha
-//                p, r -= alpha A p on the tile (x and r stay in memory, read
-//                and written by their owner only); partial of |r|^2.
+//                neighbours' published edges; A p = M u + sigma p, r -= alpha
+//                A p on the tile (x and r stay in memory, read and written by
+//                their owner only); partial of |r|^2. x += alpha p waits for
+//                the next first half, where it joins the loads of r (and for
+//                the exit, after the last iteration).
 //                                                          -- grid barrier --
 // The padding slices that lie beyond t = nt - 1 or before t = 0 hold the
 // anti-periodic continuation (negated values), so the time hops carry no
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
                     float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
                     unsigned expect) {
   extern __shared__ float2 s_tile[];
-  __shared__ float s_a;
+  __shared__ float s_a, s_ap;
   __shared__ int s_stop;
   const int n = g.n, m = g.m, nt = g.nt, H = g.H;
   const int bj = blockIdx.x % rt.tiles_j, bt = blockIdx.x / rt.tiles_j;
@@ -123,10 +125,22 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       }
       beta = first ? 0.f : rr / rr_prev;
       s_a = beta;
+      s_ap = alpha;  // the previous iteration's alpha: x += alpha p is applied here
       s_stop = done;
     }
     __syncthreads();
-    if (s_stop) break;
+    const float fap = s_ap;
+    if (s_stop) {
+      // the last iteration's x update, still pending
+      if (act && fap != 0.f)
+        for_rows([&](int, int, int b, int k) {
+          const float2 pa = pA[b], pb = pB[b + NJ + n];
+          float2 xa = x[k], xb = x[H + k];
+          x[k] = make_float2(fmaf(fap, pa.x, xa.x), fmaf(fap, pa.y, xa.y));
+          x[H + k] = make_float2(fmaf(fap, pb.x, xb.x), fmaf(fap, pb.y, xb.y));
+        });
+      break;
+    }
     const float fb = s_a;
     float2* Pcur = (iter & 1) ? P1 : P0;        // this iteration's published p edges
     const float2* Pold = (iter & 1) ? P0 : P1;  // the previous iteration's
@@ -163,6 +177,12 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       // the tile's own p, in place; its edges published for the neighbours
       for_rows([&](int jj, int tt, int b, int k) {
         const float2 ra = __ldcg(r + k), rb = __ldcg(r + H + k);
+        if (fap != 0.f) {  // x += alpha p with the previous iteration's p, still in place
+          const float2 pa = pA[b], pb = pB[b + NJ + n];
+          const float2 xa = x[k], xb = x[H + k];
+          x[k] = make_float2(fmaf(fap, pa.x, xa.x), fmaf(fap, pa.y, xa.y));
+          x[H + k] = make_float2(fmaf(fap, pb.x, xb.x), fmaf(fap, pb.y, xb.y));
+        }
         float2& qa = pA[b];
         float2& qb = pB[b + NJ + n];
         float2 a = ra, c = rb;
@@ -263,13 +283,9 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
         oa.im = fmaf(sigma, pa.y, oa.im);
         ob.re = fmaf(sigma, pb.x, ob.re);
         ob.im = fmaf(sigma, pb.y, ob.im);
-        float2 xa = x[k], xb = x[H + k], ra = r[k], rb = r[H + k];
-        xa = make_float2(fmaf(fa, pa.x, xa.x), fmaf(fa, pa.y, xa.y));
-        xb = make_float2(fmaf(fa, pb.x, xb.x), fmaf(fa, pb.y, xb.y));
+        float2 ra = r[k], rb = r[H + k];
         ra = make_float2(fmaf(-fa, oa.re, ra.x), fmaf(-fa, oa.im, ra.y));
         rb = make_float2(fmaf(-fa, ob.re, rb.x), fmaf(-fa, ob.im, rb.y));
-        x[k] = xa;
-        x[H + k] = xb;
         r[k] = ra;
         r[H + k] = rb;
         loc = fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, loc))));
@@ -337,7 +353,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
                      CGScal* sc, float2* __restrict__ partA, float2* __restrict__ partB, GridBar* gb, long long limit,
                      unsigned expect) {
   extern __shared__ float4 s_tile4[];
-  __shared__ float s_a;
+  __shared__ float s_a, s_ap;
   __shared__ int s_stop;
   // all sizes and indices in cell pairs
   const int n2 = g.n >> 1, m = g.m, nt = g.nt, H2 = g.H >> 1, V2 = g.V >> 1;
@@ -396,10 +412,22 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       }
       beta = first ? 0.f : rr / rr_prev;
       s_a = beta;
+      s_ap = alpha;  // the previous iteration's alpha: x += alpha p is applied here
       s_stop = done;
     }
     __syncthreads();
-    if (s_stop) break;
+    const float fap = s_ap;
+    if (s_stop) {
+      // the last iteration's x update, still pending
+      if (act && fap != 0.f)
+        for_rows([&](int, int, int b, int k) {
+          const float4 pa = pA[b], pb = pB[b + NJ + n2];
+          float4 xa = x[k], xb = x[H2 + k];
+          x[k] = make_float4(fmaf(fap, pa.x, xa.x), fmaf(fap, pa.y, xa.y), fmaf(fap, pa.z, xa.z), fmaf(fap, pa.w, xa.w));
+          x[H2 + k] = make_float4(fmaf(fap, pb.x, xb.x), fmaf(fap, pb.y, xb.y), fmaf(fap, pb.z, xb.z), fmaf(fap, pb.w, xb.w));
+        });
+      break;
+    }
     const float fb = s_a;
     float4* Pcur = (iter & 1) ? P1 : P0;
     const float4* Pold = (iter & 1) ? P0 : P1;
@@ -434,6 +462,12 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       }
       for_rows([&](int jj, int tt, int b, int k) {
         const float4 ra = __ldcg(r + k), rb = __ldcg(r + H2 + k);
+        if (fap != 0.f) {  // x += alpha p with the previous iteration's p, still in place
+          const float4 pa = pA[b], pb = pB[b + NJ + n2];
+          const float4 xa = x[k], xb = x[H2 + k];
+          x[k] = make_float4(fmaf(fap, pa.x, xa.x), fmaf(fap, pa.y, xa.y), fmaf(fap, pa.z, xa.z), fmaf(fap, pa.w, xa.w));
+          x[H2 + k] = make_float4(fmaf(fap, pb.x, xb.x), fmaf(fap, pb.y, xb.y), fmaf(fap, pb.z, xb.z), fmaf(fap, pb.w, xb.w));
+        }
         float4& qa = pA[b];
         float4& qb = pB[b + NJ + n2];
         float4 a = ra, c = rb;
@@ -548,15 +582,11 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
                                        fmaf(sigma, pa.w, oa1.im));
         const float4 apb = make_float4(fmaf(sigma, pb.x, ob0.re), fmaf(sigma, pb.y, ob0.im), fmaf(sigma, pb.z, ob1.re),
                                        fmaf(sigma, pb.w, ob1.im));
-        float4 xa = x[k], xb = x[H2 + k], ra = r[k], rb = r[H2 + k];
-        xa = make_float4(fmaf(fa, pa.x, xa.x), fmaf(fa, pa.y, xa.y), fmaf(fa, pa.z, xa.z), fmaf(fa, pa.w, xa.w));
-        xb = make_float4(fmaf(fa, pb.x, xb.x), fmaf(fa, pb.y, xb.y), fmaf(fa, pb.z, xb.z), fmaf(fa, pb.w, xb.w));
+        float4 ra = r[k], rb = r[H2 + k];
         ra = make_float4(fmaf(-fa, apa.x, ra.x), fmaf(-fa, apa.y, ra.y), fmaf(-fa, apa.z, ra.z),
                          fmaf(-fa, apa.w, ra.w));
         rb = make_float4(fmaf(-fa, apb.x, rb.x), fmaf(-fa, apb.y, rb.y), fmaf(-fa, apb.z, rb.z),
                          fmaf(-fa, apb.w, rb.w));
-        x[k] = xa;
-        x[H2 + k] = xb;
         r[k] = ra;
         r[H2 + k] = rb;
         loc = fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, loc))));

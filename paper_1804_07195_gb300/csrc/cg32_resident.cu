@@ -50,6 +50,30 @@ struct ResTile {
 };
 
 constexpr int kResMaxThreads = 1024;
+// at most this many tiles (one block each): the partial sums below load up to
+// kResMaxTiles / 32 partials per lane of warp 0
+constexpr int kResMaxTiles = 256;
+
+// Sum of G <= kResMaxTiles float-float partials by warp 0 alone, in a fixed
+// order; valid in thread 0. Every lane issues all of its loads before the
+// first addition, and no block-wide barrier is needed: the other warps go on
+// to the next phase's loads meanwhile.
+__device__ __forceinline__ float2 ff_warp0_sum(const float2* __restrict__ part, int G) {
+  constexpr int L = kResMaxTiles / 32;
+  float2 w[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int b = threadIdx.x + 32 * j;
+    w[j] = b < G ? __ldcg(part + b) : make_float2(0.f, 0.f);
+  }
+  float2 v = w[0];
+#pragma unroll
+  for (int j = 1; j < L; ++j) v = ff_add(v, w[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+  return v;
+}
 
 __global__ void __launch_bounds__(kResMaxThreads, 1)
     k_cg32_resident(Geo g, ResTile rt, Phase<float> ph, float2* __restrict__ x, float2* __restrict__ r,
@@ -230,8 +254,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       break;
     }
     // ---- second half
-    {
-      const float2 tot = ff_sum_partials(partA, gridDim.x);
+    if (threadIdx.x < 32) {
+      const float2 tot = ff_warp0_sum(partA, gridDim.x);
       if (threadIdx.x == 0) {
         pAp = tot.x + tot.y;
         const bool bad = !(pAp > 0.f) || !isfinite(pAp);
@@ -299,8 +323,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       done = CG_TIMEOUT;
       break;
     }
-    {
-      const float2 tot = ff_sum_partials(partB, gridDim.x);
+    if (threadIdx.x < 32) {
+      const float2 tot = ff_warp0_sum(partB, gridDim.x);
       if (threadIdx.x == 0) {
         rr_prev = rr;
         rr = tot.x + tot.y;
@@ -522,8 +546,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       break;
     }
     // ---- second half
-    {
-      const float2 tot = ff_sum_partials(partA, gridDim.x);
+    if (threadIdx.x < 32) {
+      const float2 tot = ff_warp0_sum(partA, gridDim.x);
       if (threadIdx.x == 0) {
         pAp = tot.x + tot.y;
         const bool bad = !(pAp > 0.f) || !isfinite(pAp);
@@ -601,8 +625,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1)
       done = CG_TIMEOUT;
       break;
     }
-    {
-      const float2 tot = ff_sum_partials(partB, gridDim.x);
+    if (threadIdx.x < 32) {
+      const float2 tot = ff_warp0_sum(partB, gridDim.x);
       if (threadIdx.x == 0) {
         rr_prev = rr;
         rr = tot.x + tot.y;
@@ -651,7 +675,7 @@ static bool res_plan(const hmc_ctx* c, const Geo& g, bool pairs, ResTile* out, s
       if (sm > cap) break;  // larger T only grows it
       const int tj = (g.m + J - 1) / J, tt = (g.nt + T - 1) / T;
       const long long tiles = (long long)tj * tt;
-      if (tiles > c->nsm || 2 * tiles > cg32_part_capacity(c)) continue;
+      if (tiles > c->nsm || tiles > kResMaxTiles || 2 * tiles > cg32_part_capacity(c)) continue;
       const long long cells = (long long)J * T * g.n;
       const double halo = (double)(J + T) / ((double)J * T);
       if (!found || cells < best_cells || (cells == best_cells && halo < best_halo)) {

@@ -151,7 +151,7 @@ __global__ void kb_phase(const BSys* __restrict__ sys, const int* __restrict__ b
     double x = S_.phi[k], s, c;
     sincos(x, &s, &c);
     E[S_.off + k] = make_double2(c, s);
-    phi32[S_.off + k] = (float)x;
+    phi32[S_.off + k] = phi_to_f32(x);
   }
 }
 

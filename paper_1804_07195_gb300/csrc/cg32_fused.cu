@@ -59,9 +59,8 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// e^{i phi} from phi rounded to float: reduction to [-pi, pi], hardware sine and cosine
+// e^{i phi} from phi in [-pi, pi] as float (phi_to_f32): hardware sine and cosine
 __device__ __forceinline__ Cx<float> phase_f(float x) {
-  x = fmaf(-6.28318530717958648f, rintf(x * 0.159154943091895336f), x);
   float s, c;
   __sincosf(x, &s, &c);
   return Cx<float>{c, s};

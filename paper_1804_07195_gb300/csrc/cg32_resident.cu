@@ -362,11 +362,9 @@ __device__ __forceinline__ float sq4(const float4& v) { return v.x * v.x + v.y *
 // e^{i phi} of the two cells of the pair at pair index kp
 __device__ __forceinline__ void phases2(const float* __restrict__ phi32, int kp, Cx<float>& e0, Cx<float>& e1) {
   const float2 f = __ldg(reinterpret_cast<const float2*>(phi32) + kp);
-  float x0 = fmaf(-6.28318530717958648f, rintf(f.x * 0.159154943091895336f), f.x);
-  float x1 = fmaf(-6.28318530717958648f, rintf(f.y * 0.159154943091895336f), f.y);
   float s0, c0, s1, c1;
-  __sincosf(x0, &s0, &c0);
-  __sincosf(x1, &s1, &c1);
+  __sincosf(f.x, &s0, &c0);
+  __sincosf(f.y, &s1, &c1);
   e0 = Cx<float>{c0, s0};
   e1 = Cx<float>{c1, s1};
 }

@@ -313,6 +313,16 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, long
 }
 
 // ---------------------------------------------------------------------------
+// The FP32 kernels' copy of the field: phi reduced to [-pi, pi] in FP64, then
+// rounded to float. The kernels evaluate e^{i phi} from it with the hardware
+// sine and cosine, whose error bound is stated for that interval, and need
+// no reduction of their own; a field of any size keeps the float's full
+// relative precision on its phase.
+__device__ __forceinline__ float phi_to_f32(double x) {
+  return (float)fma(-6.283185307179586, rint(x * 0.15915494309189535), x);
+}
+
+// ---------------------------------------------------------------------------
 // Float-float sums for the FP32 kernels. GB300 executes FP64 at 1/58 of the FP32
 // rate, so the single-precision kernels keep their reductions off the FP64
 // pipe: a value is an unevaluated pair (hi, lo) of floats, and two pairs add

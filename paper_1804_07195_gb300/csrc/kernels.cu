@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_phase(int N, const double* __restr
     double x = phi[k];
     sincos(x, &s, &co);
     E[k] = make_double2(co, s);
-    phi32[k] = (float)x;
+    phi32[k] = phi_to_f32(x);
   }
 }
 
@@ -413,14 +413,12 @@ __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
 }
 __device__ __forceinline__ float norm4(float4 v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
 
-// e^{i phi} of the two cells of the pair at k (phi as float pairs).
+// e^{i phi} of the two cells of the pair at k (phi as float pairs, in [-pi, pi]).
 __device__ __forceinline__ void phase2(const float* phi32, int k, Cx<float>& e0, Cx<float>& e1) {
   const float2 f = *reinterpret_cast<const float2*>(phi32 + k);
-  float x0 = fmaf(-6.28318530717958648f, rintf(f.x * 0.159154943091895336f), f.x);
-  float x1 = fmaf(-6.28318530717958648f, rintf(f.y * 0.159154943091895336f), f.y);
   float s0, c0, s1, c1;
-  __sincosf(x0, &s0, &c0);
-  __sincosf(x1, &s1, &c1);
+  __sincosf(f.x, &s0, &c0);
+  __sincosf(f.y, &s1, &c1);
   e0 = Cx<float>{c0, s0};
   e1 = Cx<float>{c1, s1};
 }

@@ -34,10 +34,8 @@ template <>
 struct Phase<float> {
   const float* phi;
   __device__ __forceinline__ Cx<float> operator()(int k) const {
-    float x = phi[k];
-    x = fmaf(-6.28318530717958648f, rintf(x * 0.159154943091895336f), x);
     float s, c;
-    __sincosf(x, &s, &c);
+    __sincosf(phi[k], &s, &c);  // phi in [-pi, pi] (phi_to_f32)
     return Cx<float>{c, s};
   }
 };

@@ -48,7 +48,7 @@ def test_fused_fp64_matches_oracle(shape, ms, sigma):
 
 # FP32 tiles of the kernel with two cells per thread (Ti even): a wide tile,
 # ragged ones, the smallest (one pair, one row, one slice) and a tall one
-PAIR_TILES = [(60, 4, 16, 2), (4, 3, 5, 6), (2, 1, 1, 2), (28, 14, 64, 2), (10, 2, 3, 6)]
+PAIR_TILES = [(60, 4, 16, 2), (4, 3, 5, 6), (2, 1, 1, 2), (28, 14, 64, 2), (10, 2, 3, 6), (28, 6, 5, 6)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)

@@ -45,6 +45,36 @@ def test_apply_fp32(shape):
         assert rel_max(host(ctx.apply_MMdag(phi, ms, b, 0.2)), of.apply_MMdag(ol, w.phi, ms, bq, 0.2)) <= 1e-5
 
 
+def test_fp32_phases_of_any_size():
+    """phi shifted by 2 pi K (|K| up to 3000, so |phi| up to about 19000) is the
+    same field (Eq. ferm_op takes phi only through e^{i phi}): the FP32
+    operators, both designs of M M^dagger and the resident CG's iterates keep
+    their tolerances, since the float copy of phi is reduced to [-pi, pi] in
+    FP64 before rounding (a float rounding of phi itself would misplace each
+    phase by up to 1e-3 there)."""
+    need_gpu()
+    w = W.small(12, 12, 32, seed=210)
+    ol = OLat.from_params(w.lat)
+    K = np.random.default_rng(211).integers(-3000, 3001, size=w.phi.shape)
+    phi_big = w.phi + 2.0 * np.pi * K
+    ms = 0.4
+    bq = w.b.astype(np.complex64).astype(np.complex128)
+    with ctx_for(w.lat) as ctx:
+        phi, b = dev(phi_big), dev(w.b.astype(np.complex64))
+        assert rel_max(host(ctx.apply_M(phi, ms, b)), of.apply_M(ol, phi_big, ms, bq)) <= 5e-6
+        assert rel_max(host(ctx.apply_Mdag(phi, ms, b)), of.apply_Mdag(ol, phi_big, ms, bq)) <= 5e-6
+        ref = of.apply_MMdag(ol, phi_big, ms, bq, 0.2)
+        for variant in (1, 2):
+            ctx.set_apply_variant(variant)
+            assert rel_max(host(ctx.apply_MMdag(phi, ms, b, 0.2)), ref) <= 1e-5, variant
+        ctx.set_cg_variant(7)
+        x, info = ctx.solve_spcg(phi, ms, b, sigma=0.0, tol=1e-30, maxit=3, allow_fail=True)
+    from oracle import solvers as osv
+    ref = osv.cg(lambda v: of.apply_MMdag(ol, phi_big, ms, v, 0.0), bq, tol=1e-30, maxit=3)
+    assert info["iters"] == 3 and ref.iters == 3
+    assert rel_max(host(x).astype(np.complex128), ref.x) <= 6e-5
+
+
 def test_loaded_field_matches_explicit_field():
     need_gpu()
     w = W.workload("L6x6x16")

@@ -380,9 +380,13 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
   const int TXP = fs.Ti / 2 + 2, TY = fs.Tj + 2, NT = TXP * TY;
   float4* SA = (float4*)smem_raw;  // [S][NT] p_A pairs
   float4* SB = SA + S * NT;        // [S][NT] p_B pairs
-  float4* UA = SB + S * NT;        // [NT]    u_A(t)
-  float4* UB = UA + NT;            // [2][NT] u_B(t), u_B(t+1)
-  float2* PA = (float2*)(UB + 2 * NT);  // [S][NT] phi_A pairs
+  // u in halves (first cells, second cells): the i-neighbours read one half
+  // of a pair, which from 16-byte pairs would take twice its wavefronts
+  float2* UAl = (float2*)(SB + S * NT);  // [NT]    u_A(t), first cells
+  float2* UAh = UAl + NT;                // [NT]    second cells
+  float2* UBl = UAh + NT;                // [2][NT] u_B(t), u_B(t+1), first cells
+  float2* UBh = UBl + 2 * NT;            // [2][NT] second cells
+  float2* PA = UBh + 2 * NT;             // [S][NT] phi_A pairs
   float2* PB = PA + S * NT;             // [S][NT] phi_B pairs
 
   const int tid = threadIdx.x;
@@ -485,7 +489,8 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
       const Cx<float> u1 = hopsum_x2(cfma(Cx<float>{ea_n1.re - dm, -ea_n1.im}, hi_c(pAn), Cx<float>{-pAc.z, -pAc.w}),
                                      ndk, hi_c(pBc), lo_c(pBc), hi_c(up));
       uA = pack4(u0, u1);
-      UA[tid] = uA;
+      UAl[tid] = make_float2(u0.re, u0.im);
+      UAh[tid] = make_float2(u1.re, u1.im);
     }
     if (need_uB) {
       // u_B(t+1) = p_B(t+1) + (dm - e^{i phi_B(t)}) p_B(t) - dk [p_A(i,j) + p_A(i+1,j) + p_A(i,j+1)](t+1)
@@ -497,15 +502,18 @@ __global__ void __launch_bounds__(kPairMaxThreads, 3) k_mmdag_fused_pairs(Geo g,
       const Cx<float> u1 = hopsum_x2(cfma(Cx<float>{dm - eb_c1.re, -eb_c1.im}, hi_c(pBc), hi_c(pBn)), ndk,
                                      hi_c(pAn), right, hi_c(down));
       uBn = pack4(u0, u1);
-      UB[((J + 1) & 1) * NT + tid] = uBn;
+      UBl[((J + 1) & 1) * NT + tid] = make_float2(u0.re, u0.im);
+      UBh[((J + 1) & 1) * NT + tid] = make_float2(u1.re, u1.im);
     }
     if constexpr (OUT) {
       __syncthreads();
       if (in_tile) {
-        const float4* UBc = UB + (J & 1) * NT;
+        const int KB = (J & 1) * NT;  // u_B(t)
         // of the left pair only its second cell, of the right pair only its first is read
-        const Cx<float> bl = hi_of(UBc + nim), ar = lo_of(UA + nip);
-        const float4 bu = UBc[njm], ad = UA[njp];
+        const float2 blh = UBh[KB + nim], arl = UAl[nip];
+        const Cx<float> bl{blh.x, blh.y}, ar{arl.x, arl.y};
+        const float2 bul = UBl[KB + njm], buh = UBh[KB + njm], adl = UAl[njp], adh = UAh[njp];
+        const float4 bu = make_float4(bul.x, bul.y, buh.x, buh.y), ad = make_float4(adl.x, adl.y, adh.x, adh.y);
         // (M u)_A(t) = -u_A(t) + (e^{i phi_A(t)} - dm) u_A(t-1) - dk [u_B(i,j) + u_B(i-1,j) + u_B(i,j-1)](t)
         Cx<float> oA0 = hopsum_x2(cfma(Cx<float>{ea_c0.re - dm, ea_c0.im}, lo_c(uA_prev), Cx<float>{-uA.x, -uA.y}),
                                   ndk, lo_c(uB_cur), bl, lo_c(bu));

@@ -629,7 +629,14 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
     the algorithmic bytes per site of the operation -- what it must move: the
     vector in and out and phi (FP32: 8 + 8 + 4 = 20 B; FP64: 16 + 16 + 8 =
     40 B), the same for M, M^dagger and M M^dagger -- against the measured
-    copy peak."""
+    copy peak. On the streaming lattice the same operations are also timed
+    back to back over three rotating operand sets (x and the result: 576 MB
+    in FP32, 1.15 GB in FP64, all larger than L2 together), CUDA events
+    around 30 applications: no event gap per launch and no flush whose dirty
+    lines the application must write back, yet no operand read from L2 that
+    an earlier application left there (each application streams 240 MB,
+    and its set returns two applications later). Reported beside the
+    per-launch figures as us_back_to_back and frac_hbm_back_to_back."""
     out = {}
     per_site = {32: 20.0, 64: 40.0}
     kernels = {"M": ["apply_M_f{p}"], "Mdag": ["apply_Mdag_f{p}"],
@@ -645,6 +652,10 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
             for prec in (32, 64):
                 ct = torch.complex64 if prec == 32 else torch.complex128
                 x = torch.randn(N, dtype=ct, device="cuda")
+                xs = outs = None
+                if name.startswith("streaming"):
+                    xs = [x] + [torch.randn(N, dtype=ct, device="cuda") for _ in range(2)]
+                    outs = [torch.empty_like(x) for _ in range(3)]
                 for op in ("M", "Mdag", "MMdag_two_pass", "MMdag_fused"):
                     if op == "MMdag_two_pass":
                         ctx.set_apply_variant(1)
@@ -676,15 +687,47 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                            "frac_hbm": nbytes / t / 1e9 / hbm}
                     if op == "MMdag_fused":
                         row["tile"] = dict(zip(("Ti", "Tj", "Tt", "depth", "pairs"), ctx.fused_tile(prec)))
+                    if name.startswith("streaming"):
+                        ts = back_to_back(torch, stream, flush, op, ctx, xs, outs)
+                        row["us_back_to_back"] = ts * 1e6
+                        row["frac_hbm_back_to_back"] = nbytes / ts / 1e9 / hbm
                     rows[f"{op}_f{prec}"] = row
                 ctx.set_apply_variant(0)
-                del x
+                del x, xs, outs
         out[name] = {"sites": N, **rows}
     out["note"] = ("mean kernel time of 20 applications (CUDA events around each launch inside the library); "
-                   "the streaming lattice flushes L2 before every application; frac_hbm = algorithmic bytes "
+                   "the streaming lattice flushes L2 before every application (us, frac_hbm) and is also "
+                   "timed back to back over three rotating operand sets larger than L2 together "
+                   "(us_back_to_back, frac_hbm_back_to_back: no per-launch event gap, no flush to write "
+                   "back); frac_hbm = algorithmic bytes "
                    "(20 B/site FP32, 40 B/site FP64, also for M M^dagger) / time / measured copy peak; the "
                    "fused tile is the one the library's tuner chose for this lattice")
     return out
+
+
+def back_to_back(torch, stream, flush, op, ctx, xs, outs, reps=30):
+    """Seconds per application of op, applications back to back over the
+    rotating operand sets xs -> outs (see apply_rates)."""
+    def app(k):
+        x, o = xs[k % len(xs)], outs[k % len(xs)]
+        if op == "M":
+            ctx.apply_M(None, 0.1, x, out=o)
+        elif op == "Mdag":
+            ctx.apply_Mdag(None, 0.1, x, out=o)
+        else:
+            ctx.apply_MMdag(None, 0.1, x, out=o)
+    for k in range(len(xs)):
+        app(k)
+    flush.zero_()
+    for _ in range(16):  # a head start of GPU work, so that the host queues ahead of the GPU
+        flush.zero_()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(reps):
+        app(k)
+    z.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) * 1e-3 / reps
 
 
 def batched_solve_times(hmc, W, torch, stream, flush):

@@ -695,6 +695,7 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                 ctx.set_apply_variant(0)
                 del x, xs, outs
         out[name] = {"sites": N, **rows}
+    out["streaming_102x102x64_x8"] = c5_times_eight(hmc, W, torch, stream, flush, hbm, per_site)
     out["note"] = ("mean kernel time of 20 applications (CUDA events around each launch inside the library); "
                    "the streaming lattice flushes L2 before every application (us, frac_hbm) and is also "
                    "timed back to back over three rotating operand sets larger than L2 together "
@@ -703,6 +704,65 @@ def apply_rates(hmc, W, torch, stream, flush, hbm):
                    "(20 B/site FP32, 40 B/site FP64, also for M M^dagger) / time / measured copy peak; the "
                    "fused tile is the one the library's tuner chose for this lattice")
     return out
+
+
+def c5_times_eight(hmc, W, torch, stream, flush, hbm, per_site, copies=8, reps=32):
+    """The benchmark lattice (102x102x64) streamed from HBM: eight contexts,
+    each with its own field phi and its own vectors (together larger than L2:
+    213 MB in FP32, 426 MB in FP64), applied round-robin back to back, CUDA
+    events around `reps` applications; each context's tile and M M^dagger
+    design are its own tuner's. Counted at the same algorithmic bytes per
+    site as the other rows."""
+    n, m, nt = 102, 102, 64
+    lat = hmc.Lattice(n, m, nt, 1.0, 3.8, 12.0)
+    N = lat.nsites
+    rows = {}
+    ctxs, phis = [], []
+    try:
+        for c in range(copies):
+            g = W.rng(9100 + c)
+            phis.append(torch.tensor(g.normal(0.0, math.sqrt(lat.delta * 3.8), N), device="cuda"))
+            ctx = hmc.Context(lat)
+            ctx.load_field(phis[-1])
+            ctxs.append(ctx)
+        for prec in (32, 64):
+            ct = torch.complex64 if prec == 32 else torch.complex128
+            xs = [torch.randn(N, dtype=ct, device="cuda") for _ in range(copies)]
+            outs = [torch.empty_like(xs[0]) for _ in range(copies)]
+            for op in ("M", "Mdag", "MMdag_two_pass", "MMdag_fused"):
+                def app(k):
+                    ctx, x, o = ctxs[k % copies], xs[k % copies], outs[k % copies]
+                    if op == "M":
+                        ctx.apply_M(None, 0.1, x, out=o)
+                    elif op == "Mdag":
+                        ctx.apply_Mdag(None, 0.1, x, out=o)
+                    else:
+                        ctx.apply_MMdag(None, 0.1, x, out=o)
+                for ctx in ctxs:
+                    ctx.set_apply_variant({"MMdag_two_pass": 1, "MMdag_fused": 2}.get(op, 0))
+                for k in range(2 * copies):  # tunes each context, then warms
+                    app(k)
+                for _ in range(16):
+                    flush.zero_()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for k in range(reps):
+                    app(k)
+                z.record(stream)
+                torch.cuda.synchronize()
+                t = a.elapsed_time(z) * 1e-3 / reps
+                nbytes = per_site[prec] * N
+                row = {"us": t * 1e6, "gsite_s": N / t / 1e9, "gb_s": nbytes / t / 1e9, "frac_hbm": nbytes / t / 1e9 / hbm}
+                if op == "MMdag_fused":
+                    row["tile"] = dict(zip(("Ti", "Tj", "Tt", "depth", "pairs"), ctxs[0].fused_tile(prec)))
+                rows[f"{op}_f{prec}"] = row
+            del xs, outs
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+    return {"sites": N, "copies": copies, **rows,
+            "note": "eight independent 102x102x64 fields and vector sets applied round-robin back to back "
+                    "(working set larger than L2); CUDA events around %d applications" % reps}
 
 
 def back_to_back(torch, stream, flush, op, ctx, xs, outs, reps=30):

@@ -710,9 +710,12 @@ static hmc_status tune_fused(hmc_ctx* c, const Geo& g, R dm, R sigma, const V2<R
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
   const size_t vb = sizeof(V2<R>) * (size_t)g.N;
-  const bool cold = (2 * vb + (sizeof(R) == 4 ? 4 : 16) * (size_t)g.N) > (size_t)l2;
+  bool cold = (2 * vb + (sizeof(R) == 4 ? 4 : 16) * (size_t)g.N) > (size_t)l2;
   void* scratch = nullptr;
-  if (cold) HMC_TRY(ws_get(c, sizeof(R) == 4 ? WS_U32 : WS_U64, vb, &scratch));
+  if (cold && ws_get(c, sizeof(R) == 4 ? WS_U32 : WS_U64, vb, &scratch) != HMC_OK) {
+    cold = false;  // no room for the scratch vector: the candidates are timed back to back
+    c->err.clear();
+  }
   cudaEvent_t ev[2][5];
   for (auto& row : ev)
     for (auto& e : row) HMC_CUDA(c, cudaEventCreate(&e));

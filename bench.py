@@ -420,9 +420,10 @@ def main():
                             "iteration (the CG step's operator with its dot, x and r updates with the norm, p "
                             "update, complex64) times the iterations the solve ran, although p and M^dagger p "
                             "stay in shared memory and r, x in L2 (1.33M sites: the working set fits the 126 MB "
-                            "L2), hence a fraction near or above 1 of the copy peak; 'traffic' is null: the DRAM "
-                            "bytes of such a launch are its first cold reads (ncu, 60 iterations: 27 MB read, "
-                            "4.5 MB written), not a per-iteration figure")
+                            "L2), hence a fraction near or above 1 of the copy peak; 'traffic' is the DRAM bytes "
+                            "of one launch under ncu (one 60-iteration solve on this lattice, caches flushed "
+                            "first): its cold first reads of r, x, b and phi and the final writes, which do not "
+                            "grow with the iterations a launch runs, so far below the algorithmic bytes")
     else:
         roofline["note"] = ("the FP32 CG working set (59 MB) stays in L2 between iterations; 'traffic' is the "
                             "cold-cache DRAM bytes of one launch under ncu (the algorithmic reads); with warm "
@@ -1102,6 +1103,7 @@ FUSED_STREAM_TILE = (28, 14, 22, 2, 1)
 # the translation units of the FP32 CG kernels whose DRAM traffic
 # profiles/traffic.json records, and everything they include
 PAIR_SOURCES = ("paper_1804_07195_gb300/csrc/kernels.cu", "paper_1804_07195_gb300/csrc/cg32_fused.cu",
+                "paper_1804_07195_gb300/csrc/cg32_resident.cu",
                 "paper_1804_07195_gb300/csrc/kernels.h", "paper_1804_07195_gb300/csrc/ctx.h",
                 "paper_1804_07195_gb300/csrc/common.cuh", "paper_1804_07195_gb300/csrc/operator.cuh",
                 "paper_1804_07195_gb300/csrc/launch.cuh", "include/hmc.h")
@@ -1109,7 +1111,8 @@ PAIR_SOURCES = ("paper_1804_07195_gb300/csrc/kernels.cu", "paper_1804_07195_gb30
 # (profile name, design) of a CG kernel -> its CUDA function
 TRAFFIC_FUNCS = {("cg_pMdag_f32", 0): "k_cg32_pmdag", ("cg_M_update_f32", 0): "k_cg32_m",
                  ("cg_pMdag_f32", 4): "k_cg32_pmdag2", ("cg_M_update_f32", 4): "k_cg32_m2",
-                 ("cg1_fused_f32", 0): "k_cg32_fused1"}
+                 ("cg1_fused_f32", 0): "k_cg32_fused1", ("cg_resident_f32", 0): "k_cg32_resident",
+                 ("cg_resident_f32", 4): "k_cg32_resident2"}
 
 
 def kernel_source_sha():

@@ -31,7 +31,7 @@ def test_scaled_units_are_refused():
 
 
 def test_every_traffic_function_has_a_profile_name():
-    assert set(bench.TRAFFIC_FUNCS.values()) >= {"k_cg32_pmdag", "k_cg32_m", "k_cg32_fused1"}
+    assert set(bench.TRAFFIC_FUNCS.values()) >= {"k_cg32_pmdag", "k_cg32_m", "k_cg32_fused1", "k_cg32_resident2"}
     for f in bench.PAIR_SOURCES:
         assert os.path.exists(os.path.join(bench.ROOT, f)), f
 

@@ -327,7 +327,11 @@ __global__ void __launch_bounds__(fused_max_threads<R>()) k_mmdag_fused(Geo g, F
 // neighbouring thread's slot. The box is Ti + 4 cells wide (cells i0 - 2 to
 // i0 + Ti + 1, Ti even: pairs stay aligned) and Tj + 2 rows high; the cells
 // i0 - 1 and i0 + Ti are the ring, the outermost two columns only feed them.
-// Same two-barrier step as k_mmdag_fused otherwise (Eq. ferm_op rows as there).
+// Each step has two block barriers: one publishes the arrived slice, the
+// other the u values the step formed, and the step's output follows it (no
+// lag, so u_A is single-buffered and u_B double-buffered). u is kept as
+// first-cell and second-cell halves, since the i-neighbours read one half
+// of a pair. Eq. ferm_op rows as in k_mmdag_fused.
 __device__ __forceinline__ Cx<float> lo_c(const float4& v) { return Cx<float>{v.x, v.y}; }
 __device__ __forceinline__ Cx<float> hi_c(const float4& v) { return Cx<float>{v.z, v.w}; }
 __device__ __forceinline__ float4 pack4(Cx<float> a, Cx<float> b) { return make_float4(a.re, a.im, b.re, b.im); }

@@ -46,6 +46,9 @@ def test_resident_iterates_equal_cg(shape, ms, sigma):
         assert st["launches"] >= 2
         # two cells per thread (16-byte pairs) where n is even
         assert st["design"] == (4 if shape[0] % 2 == 0 else 0)
+        # the roofline's algorithmic bytes: 96 B per site for exactly the
+        # iterations that ran, whatever the launches
+        assert st["bytes"] == 96.0 * w.lat.nsites * sum(sorted({1, 2, kmax}))
 
 
 def test_resident_iterates_at_full_size():
@@ -58,7 +61,8 @@ def test_resident_iterates_at_full_size():
     with ctx_for(w.lat) as ctx:
         ctx.set_cg_variant(7)
         x, info = ctx.solve_spcg(dev(w.phi), 0.1, dev(b32), tol=1e-30, maxit=3, allow_fail=True)
-        assert ctx.profile_read()["cg_resident_f32"]["launches"] >= 1
+        st = ctx.profile_read()["cg_resident_f32"]
+        assert st["launches"] >= 1 and st["bytes"] == 96.0 * w.lat.nsites * 3
     ref = osv.cg(lambda v: of.apply_MMdag(ol, w.phi, 0.1, v), b32.astype(np.complex128), tol=1e-30, maxit=3)
     assert info["iters"] == 3
     assert rel_max(host(x).astype(np.complex128), ref.x) <= 1e-4

@@ -34,13 +34,13 @@ struct BSys {
   double dm, sigma;
   const double* phi; // the caller's field (phase kernel only)
   int maxit;         // iteration limit of this system's CG
-  int pad;
+  float dm32, sigma32;  // dm and sigma rounded to float for the FP32 kernels
 };
 
 struct BState {
   CGScal cg;
   int active;  // 1 while the system takes part in the current inner solve
-  int pad;
+  float alpha32, beta32;  // cg.alpha and cg.beta rounded to float, written once per system
 };
 
 // Sum K values over the blocks [base, base + count) of one system, in a fixed
@@ -116,10 +116,23 @@ __device__ __forceinline__ bool group_finish(double blocktot, double* partials, 
   return true;
 }
 
-// Scalars of a system in the compute precision, formed once per block.
+// Scalars of a system in the compute precision, read once per block by
+// thread 0: the FP32 kernels read float copies written once per system, so
+// no block waits on FP64 conversions (slow on this GPU) in its prologue.
 template <typename R>
 struct BScal {
   R dm, sigma, coef;
+  static __device__ __forceinline__ void from(const BSys& S, const BState& st, bool alpha, BScal* out) {
+    if constexpr (sizeof(R) == 4) {
+      out->dm = S.dm32;
+      out->sigma = S.sigma32;
+      out->coef = alpha ? st.alpha32 : st.beta32;
+    } else {
+      out->dm = S.dm;
+      out->sigma = S.sigma;
+      out->coef = alpha ? st.cg.alpha : st.cg.beta;
+    }
+  }
 };
 
 #define BLOCK_SYS()                                  \
@@ -196,6 +209,7 @@ __global__ void kb_init(const BSys* __restrict__ sys, const int* __restrict__ bs
     c.iter = 0;
     c.maxit = min(maxit, S_.maxit);
     c.alpha = c.beta = c.pAp = 0.0;
+    bst[s_].alpha32 = bst[s_].beta32 = 0.f;
     c.done = (!bst[s_].active || tot[0] <= c.thresh) ? CG_CONVERGED : CG_RUNNING;
     if (!isfinite(tot[0])) c.done = CG_BREAKDOWN;
   }
@@ -215,9 +229,7 @@ __device__ __forceinline__ void pmdag_body(int vb, const BSys* __restrict__ sys,
   __shared__ int skip;
   if (threadIdx.x == 0) {
     skip = bst[s_].cg.done;
-    sc.dm = (R)S_.dm;
-    sc.sigma = (R)S_.sigma;
-    sc.coef = (R)bst[s_].cg.beta;
+    BScal<R>::from(S_, bst[s_], false, &sc);
   }
   __syncthreads();
   if (skip) return;
@@ -259,6 +271,7 @@ __device__ __forceinline__ void pmdag_body(int vb, const BSys* __restrict__ sys,
     } else {
       c.alpha = c.rr / tot;
     }
+    bst[s_].alpha32 = (float)c.alpha;
   }
 }
 
@@ -284,9 +297,7 @@ __device__ __forceinline__ void m_body(int vb, const BSys* __restrict__ sys, con
   __shared__ int skip;
   if (threadIdx.x == 0) {
     skip = bst[s_].cg.done;
-    sc.dm = (R)S_.dm;
-    sc.sigma = (R)S_.sigma;
-    sc.coef = (R)bst[s_].cg.alpha;
+    BScal<R>::from(S_, bst[s_], true, &sc);
   }
   __syncthreads();
   if (skip) return;
@@ -319,6 +330,7 @@ __device__ __forceinline__ void m_body(int vb, const BSys* __restrict__ sys, con
     CGScal& c = bst[s_].cg;
     const double rr = tot;
     c.beta = rr / c.rr;
+    bst[s_].beta32 = (float)c.beta;
     c.rr = rr;
     c.iter += 1;
     if (!isfinite(rr))
@@ -857,6 +869,8 @@ extern "C" hmc_status hmc_solve_batched(hmc_ctx* c, int nsys, const hmc_system* 
     S.off = off;
     S.dm = delta * y.ms;
     S.sigma = y.sigma;
+    S.dm32 = (float)S.dm;
+    S.sigma32 = (float)S.sigma;
     S.phi = y.phi;
     S.maxit = y.maxit;
     off += N;

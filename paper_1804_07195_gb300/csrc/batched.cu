@@ -157,6 +157,27 @@ struct BScal {
   const int lb = (vb) - S_.block0;                   \
   const int stride = S_.nblocks * blockDim.x
 
+// VBLOCK_SYS for the CG iteration kernels, with the system's state: thread 0
+// issues the loads of the descriptor, the done flag and the scalars together
+// (one L2 round trip after the block's system index, not two), then one
+// barrier publishes S_, sc and skip.
+#define VBLOCK_SYS_CG(vb, ALPHA)                     \
+  __shared__ BSys S_;                                \
+  __shared__ BScal<R> sc;                            \
+  __shared__ int skip;                               \
+  const int s_ = bsys[vb];                           \
+  __syncthreads();                                   \
+  if (threadIdx.x == 0) {                            \
+    const BSys sl = sys[s_];                         \
+    skip = bst[s_].cg.done;                          \
+    BScal<R>::from(sl, bst[s_], ALPHA, &sc);         \
+    S_ = sl;                                         \
+  }                                                  \
+  __syncthreads();                                   \
+  const Geo& g = S_.g;                               \
+  const int lb = (vb) - S_.block0;                   \
+  const int stride = S_.nblocks * blockDim.x
+
 __global__ void kb_phase(const BSys* __restrict__ sys, const int* __restrict__ bsys,
                          double2* __restrict__ E, float* __restrict__ phi32) {
   BLOCK_SYS();
@@ -224,14 +245,7 @@ __device__ __forceinline__ void pmdag_body(int vb, const BSys* __restrict__ sys,
                                            const V2<R>* __restrict__ pold, V2<R>* __restrict__ pnew,
                                            V2<R>* __restrict__ u, double* partials, unsigned* tickets,
                                            unsigned* ndone) {
-  VBLOCK_SYS(vb);
-  __shared__ BScal<R> sc;
-  __shared__ int skip;
-  if (threadIdx.x == 0) {
-    skip = bst[s_].cg.done;
-    BScal<R>::from(S_, bst[s_], false, &sc);
-  }
-  __syncthreads();
+  VBLOCK_SYS_CG(vb, false);
   if (skip) return;
   const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
   const R dm = sc.dm, sigma = sc.sigma, beta = sc.coef, dk = geo_dk(g, R(0));
@@ -292,14 +306,7 @@ __device__ __forceinline__ void m_body(int vb, const BSys* __restrict__ sys, con
                                        const V2<R>* __restrict__ p, V2<R>* __restrict__ x,
                                        V2<R>* __restrict__ r, double* partials, unsigned* tickets,
                                        unsigned* ndone) {
-  VBLOCK_SYS(vb);
-  __shared__ BScal<R> sc;
-  __shared__ int skip;
-  if (threadIdx.x == 0) {
-    skip = bst[s_].cg.done;
-    BScal<R>::from(S_, bst[s_], true, &sc);
-  }
-  __syncthreads();
+  VBLOCK_SYS_CG(vb, true);
   if (skip) return;
   const Phase<R> ph = BPhase<R>::at(E, p32, S_.off);
   const R dm = sc.dm, sigma = sc.sigma, alpha = sc.coef;
